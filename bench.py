@@ -1,0 +1,361 @@
+"""Throughput of the fused VANSE lattice Boltzmann step on GB300.
+
+Workload (default): D3Q19, 256^3 periodic, FP32 storage, tau = 0.6, body
+force 1e-6 x, space-time varying volume fraction
+phi = 0.7 + 0.2 sin(2 pi x/L) cos(2 pi y/L) sin(2 pi z/L + 2 pi t/T), T = 1000
+steps, refreshed (phi_ref, d_t phi) every 10 steps.  One bench step = one
+fused time step of the whole lattice.  The populations (1.27 GB in FP32) are
+far larger than L2 (129 MB), so no flush is needed between steps.
+
+Output: one JSON line (rank 0).  ``value`` = GLUPS (10^9 cell updates per
+second) with inputs resident in HBM; ``e2e`` = the same through the C ABI
+with host buffers (phi refreshes uploaded from pinned host memory, the
+check-step statistics read back); ``roofline`` = the step kernel's
+algorithmic bytes per launch over its average CUDA-event duration, against
+the measured HBM copy bandwidth.  ``--impl reference`` times the FP64 CPU
+oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L_DEFAULT = 256
+T_PERIOD = 1000.0
+K_EPS = 10
+TAU = 0.6
+G = (1e-6, 0.0, 0.0)
+Q = 19
+METRIC = "GLUPS (D3Q19 VANSE step, 256^3, FP32)"
+
+
+def bytes_per_cell(storage: str) -> int:
+    """Algorithmic bytes per cell update: one read and one write of each
+    population (AA pattern) plus phi_ref and d_t phi, 4 B each."""
+    b = {"fp32": 4, "fp16": 2}[storage]
+    return 2 * Q * b + 4 + 4
+
+
+def peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            v = float(json.load(fh)["hbm_gbs"])
+        return v, "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def profiled_traffic(storage: str, kernel_src_hash: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel
+    source has not changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", f"step_fast_d3q19_{storage}_256.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
+    t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m or not t or m.group(1) != kernel_src_hash:
+        return None
+    return float(t.group(1))
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in ("step_fast.cuh", "step_fast_d3q19.cu", "lattice.cuh", "internal.h"):
+        with open(os.path.join(ROOT, "paper_2208_09267_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for s in self.samples for j in range(4)
+                          if s[5 + j].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def eps_fields(L, t):
+    from paper_2208_09267_gb300 import inputs
+    e, d = inputs.eps_travelling_wave(L, float(t), T=T_PERIOD)
+    return e.ravel().astype(np.float32), d.ravel().astype(np.float32)
+
+
+def run_gpu(args, rank, world):
+    import torch
+
+    from paper_2208_09267_gb300 import lbm
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    L = args.size
+    N = L ** 3
+    total_steps = args.warmup + args.steps
+    nref = (total_steps + K_EPS - 1) // K_EPS + 1
+
+    # phi_ref / d_t phi at every refresh, resident on the device and pinned on the host
+    host_e = torch.empty((nref, N), dtype=torch.float32, pin_memory=True)
+    host_d = torch.empty((nref, N), dtype=torch.float32, pin_memory=True)
+    for j in range(nref):
+        e, d = eps_fields(L, j * K_EPS)
+        host_e[j].numpy()[:] = e
+        host_d[j].numpy()[:] = d
+    dev_e = host_e.to(f"cuda:{dev}")
+    dev_d = host_d.to(f"cuda:{dev}")
+
+    def make(storage):
+        lat = lbm.Lattice("D3Q19", (L, L, L), tau=TAU, storage=storage,
+                          stream=stream.cuda_stream, block=tuple(args.block))
+        lat.set_epsilon(dev_e[0], dev_d[0], 0)
+        lat.set_force(G)
+        lat.init_equilibrium()
+        return lat
+
+    def device_run(lat, steps, timed):
+        """steps fused steps with refreshes from device memory; returns
+        (total_ms, kernel_ms, kernels) when timed."""
+        ev = []
+        n = lat.steps_done
+        done = 0
+        while done < steps:
+            k = min(K_EPS - (n % K_EPS), steps - done)
+            if timed:
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                lat.step(k)
+                b.record(stream)
+                ev.append((a, b, k))
+            else:
+                lat.step(k)
+            n += k
+            done += k
+            if n % K_EPS == 0:
+                j = n // K_EPS
+                lat.set_epsilon(dev_e[j], dev_d[j], n)
+        return ev
+
+    results = {}
+    for storage in args.storages:
+        lat = make(storage)
+        device_run(lat, args.warmup, False)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        c0 = lbm.launch_count()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(dev) as clk:
+            t0.record(stream)
+            ev = device_run(lat, args.steps, True)
+            t1.record(stream)
+            torch.cuda.synchronize()
+        launches = lbm.launch_count() - c0
+        total_ms = t0.elapsed_time(t1)
+        step_ms = sum(a.elapsed_time(b) for a, b, _ in ev)
+        nk = sum(k for _, _, k in ev)
+        if world > 1:
+            t = torch.tensor([total_ms], device=f"cuda:{dev}")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(t.item())
+        st = lat.step(1)  # one check step (not timed) to confirm the run is sane
+        if st["nan_seen"]:
+            raise RuntimeError(f"{storage}: NaN after the timed steps")
+        results[storage] = {"total_ms": total_ms, "kernel_ms": step_ms / nk, "launches": launches,
+                            "clocks": clk.summary(), "mass": st["mass"]}
+        lat.close()
+
+    # end to end through the C ABI with host buffers (FP32)
+    e2e = None
+    if not args.no_e2e:
+        lat = lbm.Lattice("D3Q19", (L, L, L), tau=TAU, storage=args.storages[0],
+                          stream=stream.cuda_stream, block=tuple(args.block))
+        lat.set_force(G)
+        he = [host_e[j].numpy() for j in range(nref)]
+        hd = [host_d[j].numpy() for j in range(nref)]
+        lat.set_epsilon(he[0], hd[0], 0)
+        lat.init_equilibrium()
+        for j in range(args.warmup // K_EPS):
+            lat.step(K_EPS)
+            lat.set_epsilon(he[j + 1], hd[j + 1], (j + 1) * K_EPS)
+        torch.cuda.synchronize()
+        n0 = lat.steps_done
+        chunks = max(1, args.steps // K_EPS)
+        t = time.perf_counter()
+        for j in range(chunks):
+            lat.step(K_EPS)                     # ends with a check step: stats D2H
+            jj = (n0 + (j + 1) * K_EPS) // K_EPS
+            lat.set_epsilon(he[jj], hd[jj], n0 + (j + 1) * K_EPS)   # H2D from pinned host
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        e2e = {"value": N * chunks * K_EPS / dt / 1e9, "unit": "GLUPS",
+               "h2d_bytes_per_step": 2 * 4 * N / K_EPS,
+               "d2h_bytes_per_step": 120 / K_EPS,
+               "note": "phi_ref and d_t phi uploaded from pinned host memory every 10 steps; "
+                       "each 10-step call reads its check statistics back"}
+        lat.close()
+    return results, e2e
+
+
+def cpu_baseline(sample_L=48, steps=None, budget_s=20.0):
+    """The FP64 oracle on the host cores, timed on a bounded sample of the
+    same workload (a sample_L^3 lattice with the same phi recipe)."""
+    import oracle
+    oracle.build()
+    oracle.set_threads(0)
+    e, d = eps_fields(sample_L, 0)
+    P = oracle.Problem("D3Q19", sample_L, sample_L, sample_L, tau=TAU, eps_ref=e, deps_dt=d,
+                       g=G)
+    f = P.init()
+    t = time.perf_counter()
+    f = P.run(f, 0, 2)
+    per = (time.perf_counter() - t) / 2
+    if steps is None:
+        steps = max(2, int(budget_s / max(per, 1e-6)))
+    t = time.perf_counter()
+    P.run(f, 2, steps)
+    dt = time.perf_counter() - t
+    cores = os.cpu_count() or 1
+    return {"value": sample_L ** 3 * steps / dt / 1e9, "unit": "GLUPS", "cores": cores,
+            "kind": "oracle",
+            "sample": f"D3Q19 {sample_L}^3 lattice, same phi recipe and tau, {steps} steps, "
+                      f"FP64 oracle with {cores} OpenMP threads ({dt:.1f} s)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--size", type=int, default=L_DEFAULT)
+    ap.add_argument("--block", type=int, nargs=2, default=[0, 0])
+    ap.add_argument("--storages", nargs="+", default=["fp32", "fp16"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    L = args.size
+    N = L ** 3
+    config = {"workload": f"D3Q19 VANSE BGK {L}^3 periodic, tau 0.6, space-time varying phi "
+                          f"(T = 1000 steps, refreshed every {K_EPS}), body force 1e-6 x",
+              "cells": N, "l2_flush": "inputs larger than L2 (populations 1.27 GB)",
+              "parallelism": f"replicas x{world}"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        cb = cpu_baseline(sample_L=48 if L >= 48 else L, budget_s=max(5.0, args.steps * 0.5))
+        line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "GLUPS",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": config, "cpu_baseline": cb,
+                "e2e": {"value": cb["value"], "unit": "GLUPS", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+
+    res, e2e = run_gpu(args, rank, world)
+    main_st = args.storages[0]
+    r = res[main_st]
+    glups = N / (r["total_ms"] / args.steps) / 1e6 * world
+    peak, peak_kind = peak_hbm()
+    bpc = bytes_per_cell(main_st)
+    achieved = bpc * N / (r["kernel_ms"] * 1e-3) / 1e9
+    src_hash = kernel_source_hash()
+    line = {
+        "metric": METRIC, "value": glups, "unit": "GLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["total_ms"] / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if main_st == "fp32" else "f16-storage/f32-compute", "data": "synthetic",
+        "config": config,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": f"{peak_kind} copy bandwidth",
+                     "traffic": profiled_traffic(main_st, src_hash),
+                     "algorithmic_bytes_per_cell": bpc,
+                     "kernel": "step_fast_kernel<D3Q19,float>", "kernel_ms": r["kernel_ms"]},
+        "gpu_launches": r["launches"], "clocks": r["clocks"], "e2e": e2e,
+    }
+    for st, rr in res.items():
+        if st == main_st:
+            continue
+        bb = bytes_per_cell(st)
+        ach = bb * N / (rr["kernel_ms"] * 1e-3) / 1e9
+        line[st] = {"value": N / (rr["total_ms"] / args.steps) / 1e6, "unit": "GLUPS",
+                    "kernel_ms": rr["kernel_ms"], "algorithmic_bytes_per_cell": bb,
+                    "achieved_gbs": ach, "frac": ach / peak, "gpu_launches": rr["launches"],
+                    "traffic": profiled_traffic(st, src_hash), "clocks": rr["clocks"]}
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(sample_L=48 if L >= 48 else L, budget_s=15.0)
+    if rank == 0:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,266 @@
+/*
+ * lbm_vanse.h -- C ABI of the GB300 (sm_103a) solver for the consistent
+ * lattice Boltzmann scheme of the volume averaged Navier-Stokes equations
+ * (VANSE) of Bukreev, Simonis, Kummerlaender, Jessberger and Krause,
+ * arXiv 2208.09267.
+ *
+ * One handle holds one lattice: its populations, its volume fraction phi
+ * (the paper's phi^flat, called epsilon here), its force fields and its time
+ * counter, all in device memory owned by the library.  Every time step is
+ * one fused CUDA kernel (Sec. 2.2): the zeroth and first moments, the
+ * quadrature of phi over the cell (eq. (quad), Table "weights"), the
+ * effective density (eq. (density)), the pressure-correction force
+ * F_PC = c_s^2 rho~ grad(phi) (eq. (pressForce)), the velocity with the Guo
+ * half-force shift (eq. (velocity)), the equilibrium with the zeroth moment
+ * in place of rho~ phi (eq. (feq)), BGK relaxation with Guo forcing and
+ * streaming (eq. (lbe)), with halfway bounce-back at walls.
+ *
+ * Conventions shared by every entry point:
+ *   - Lattice units: dx = dt = 1, c_s^2 = 1/3, nu = (tau - 1/2)/3
+ *     (Appendix A, last equation).
+ *   - Fields are dense arrays with x fastest: index (z*ny + y)*nx + x.
+ *     Vector fields are component-major: component a at offset a*N,
+ *     N = nx*ny*nz.  In 2D (D2Q9) nz = 1 and vector fields still have three
+ *     components (the third is ignored on input, zero on output).
+ *   - `on_device` = 0: pointers are host memory (pageable or pinned); the
+ *     call copies them before it returns.  `on_device` = 1: pointers are
+ *     device memory of the current device; the call reads/writes them in
+ *     stream order on the handle's stream and may return before the copy has
+ *     run: keep the buffer alive until the stream has passed that point.
+ *   - Inputs are always copied: the library keeps no caller pointer.
+ *   - Every call returns an lbm_status; on failure lbm_vanse_last_error()
+ *     gives a message.  No call aborts or exits.  A handle is not
+ *     thread-safe: serialise calls on one handle.
+ *   - All device work of a handle runs on the stream given at creation
+ *     (params.cuda_stream, NULL = the legacy default stream).
+ */
+#ifndef LBM_VANSE_H
+#define LBM_VANSE_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define LBM_API __attribute__((visibility("default")))
+#else
+#define LBM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_vanse *lbm_vanse_t;
+typedef struct lbm_vanse_batch *lbm_vanse_batch_t;
+
+/* Discrete velocity sets: D2Q9 (Table "latt_par"), D3Q27 (Table "latt_3d"),
+   D3Q19 (not in the paper; standard textbook weights 1/3, 1/18, 1/36). */
+enum lbm_lattice { LBM_D2Q9 = 0, LBM_D3Q19 = 1, LBM_D3Q27 = 2 };
+
+/* Population storage.  LBM_FP64: f_i stored and collided in double, in the
+   canonical evaluation order, bit-identical to the FP64 reference.
+   LBM_FP32: the deviation f_i/w_i - rho0*sigma stored in float, collided in
+   float.  LBM_FP16_SHIFTED: the same deviation times 2^k stored in IEEE
+   half, collided in float.  sigma is the cell's phi_ref (see set_epsilon). */
+enum lbm_storage { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16_SHIFTED = 2 };
+
+enum lbm_status {
+  LBM_OK = 0,
+  LBM_EINVAL = -1,     /* bad argument or field value */
+  LBM_ENOMEM = -2,     /* device allocation failed or HBM budget exceeded */
+  LBM_ECUDA = -3,      /* a CUDA runtime call failed */
+  LBM_EUNSTABLE = -4,  /* a check step saw NaN/Inf in the moments */
+  LBM_ETIMEOUT = -5,   /* a bounded device-side wait gave up */
+  LBM_ESTATE = -6      /* call not valid in the handle's current state */
+};
+
+/* Bits of lbm_vanse_params.walls / quad_axes: axis x = 1, y = 2, z = 4. */
+enum { LBM_AXIS_X = 1u, LBM_AXIS_Y = 2u, LBM_AXIS_Z = 4u };
+
+typedef struct {
+  int lattice;              /* enum lbm_lattice */
+  int storage;              /* enum lbm_storage */
+  int nx, ny, nz;           /* cells per axis, >= 1; nz must be 1 for D2Q9 */
+  double tau;               /* BGK relaxation time, eq. (lbe); > 0.5 */
+  double rho0;              /* reference density; p = c_s^2 (rho~ - rho0) */
+  int quad_dim;             /* row of Table "weights" (1, 2, 3); 0 = number
+                               of bits in quad_axes */
+  unsigned quad_axes;       /* axes whose face neighbours enter eq. (quad);
+                               0 = every lattice axis.  The paper picks the
+                               D1Q3/D2Q5/D3Q7 rule by the number of
+                               directions in which phi varies (Sec. 2.2). */
+  unsigned walls;           /* axes whose first and last layer are solid
+                               (halfway bounce-back); other axes periodic */
+  int fp16_scale_log2;      /* k of LBM_FP16_SHIFTED (stored = dev * 2^k);
+                               ignored for the other storages */
+  void *cuda_stream;        /* cudaStream_t for all device work, or NULL */
+  size_t hbm_budget_bytes;  /* 0 = unlimited; create fails with LBM_ENOMEM
+                               when the handle would need more */
+  int block_x, block_y;     /* thread-block shape of the one-cell-per-thread
+                               step kernel; 0 = library default */
+  int kernel;               /* step kernel: 0 = automatic, 1 = one cell per
+                               thread, 2 = row-staged (whole x-rows staged in
+                               shared memory by TMA bulk copies; needs nx a
+                               multiple of 4 (FP32) or 8 (FP16), 32 <= nx <= 512,
+                               no walls on x; LBM_EINVAL otherwise) */
+} lbm_vanse_params;
+
+/* Global sums of the state at time n (pre-collision), taken on a check step
+   in FP64 on the device.  mass = sum M0, momentum = sum (J + F/2), residual =
+   ||u^n - u^{n-K}||_2 / (K ||u^n||_2) over the cells, K = steps since the
+   previous check (-1 when there is no previous check or residual tracking
+   is off).  On a periodic lattice the Guo scheme gives sum J(n+1) -
+   sum J(n) = force, so consecutive checks also pin the momentum input. */
+typedef struct {
+  double mass;
+  double momentum[3];
+  double residual;
+  double u_norm;            /* ||u^n||_2 */
+  double force[3];          /* sum of the force sum_k F_k over the cells */
+  long long steps_done;     /* time counter n after the call */
+  long long step_of_stats;  /* the n the sums describe */
+  int nan_seen;             /* 1 if a check saw NaN or Inf */
+  int converged;            /* 1 if the residual reached residual_tol */
+} lbm_vanse_stats;
+
+/* Library version string; never NULL. */
+LBM_API const char *lbm_vanse_version(void);
+
+/* Message of the last failed call on h (h may be NULL: last failure of
+   any handle on this thread).  Never NULL; valid until the next call. */
+LBM_API const char *lbm_vanse_last_error(lbm_vanse_t h);
+
+/* Fill p with defaults: D3Q19, FP32, 32^3, tau 0.6, rho0 1, quad on every
+   axis, no walls, k = 10, default stream, no budget, default block. */
+LBM_API int lbm_vanse_params_default(lbm_vanse_params *p);
+
+/* Device bytes a handle with these parameters allocates (populations,
+   phi double buffer, d_t phi, force fields are counted as allocated
+   lazily: this is the figure without optional fields, plus the moment and
+   reduction scratch).  Used for admission by HBM budget. */
+LBM_API size_t lbm_vanse_device_bytes(const lbm_vanse_params *p, int with_deps, int with_force_field);
+
+/* Create a lattice in the rest state u = 0, p = 0 with phi = 1 everywhere:
+   f_i = w_i rho0 (eq. (equilibrium) with u = 0).  Errors: LBM_EINVAL for
+   bad parameters, LBM_ENOMEM if allocation fails or exceeds the budget,
+   LBM_ECUDA.  *out is NULL on failure. */
+LBM_API int lbm_vanse_create(const lbm_vanse_params *p, lbm_vanse_t *out);
+
+/* Release every device allocation of h (stream-ordered) and h itself.
+   NULL is accepted. */
+LBM_API void lbm_vanse_destroy(lbm_vanse_t h);
+
+/* Set the volume fraction phi(x, t) = eps_ref(x) + (t - n_ref) deps_dt(x)
+   (Sec. 2.2: phi varies in space and time; the pair is refreshed by the
+   caller, and is exact at t = n_ref).  eps_ref: N values in (0, 1];
+   deps_dt: N values or NULL for a static field.  The shift sigma of the
+   reduced-precision storages becomes eps_ref: the next step decodes with
+   the previous sigma and encodes with the new one, so no extra pass runs.
+   Errors: LBM_EINVAL if a host-side eps_ref value is not in (0, 1] or not
+   finite (device-side inputs are not validated).  The FP64 twin takes
+   doubles; on FP32/FP16 handles it rounds them to float. */
+LBM_API int lbm_vanse_set_epsilon(lbm_vanse_t h, const float *eps_ref, const float *deps_dt,
+                          long long n_ref, int on_device);
+LBM_API int lbm_vanse_set_epsilon_f64(lbm_vanse_t h, const double *eps_ref, const double *deps_dt,
+                              long long n_ref, int on_device);
+
+/* External force density: sum_k F_k = g + field(x) + (t - n_ref) dfield_dt(x)
+   + F_PC (Sec. 2.2 eq. (pressForce); Sec. 3, force sum of the manufactured
+   examples).  g: three doubles (NULL = 0).  field, dfield_dt: 3*N values or
+   NULL.  Errors: LBM_EINVAL for non-finite host values. */
+LBM_API int lbm_vanse_set_force(lbm_vanse_t h, const double *g, const float *field,
+                        const float *dfield_dt, long long n_ref, int on_device);
+LBM_API int lbm_vanse_set_force_f64(lbm_vanse_t h, const double *g, const double *field,
+                            const double *dfield_dt, long long n_ref, int on_device);
+
+/* Initial populations at the current time n (eq. (equilibrium)):
+   f_i = w_i rho~0 m(x) poly_i(u_eq) with rho~0 = rho0 + p0/c_s^2 and
+   m = phi(x, n).  mode bit 1: m = int phi dV of eq. (quad) (the paper's
+   form after the first step, eq. (feq)); bit 2: u_eq = u0 - F/(2 M0) so that
+   eq. (velocity) returns u0 at time n.  p0: N values or NULL (0); u0: 3*N or
+   NULL (0).  Solid cells are left empty. */
+LBM_API int lbm_vanse_init_equilibrium(lbm_vanse_t h, const float *p0, const float *u0, int mode,
+                               int on_device);
+LBM_API int lbm_vanse_init_equilibrium_f64(lbm_vanse_t h, const double *p0, const double *u0,
+                                   int mode, int on_device);
+
+/* Advance up to max_steps time steps (eq. (lbe)), each one fused kernel
+   launch (chunks of steps are replayed as a captured CUDA graph).  Every
+   check_every steps (0 = only the last step) and on the last step, a check
+   step also reduces mass, momentum and the velocity residual in FP64; when
+   residual_tol > 0 and the residual falls to it, the call stops early.
+   out (may be NULL) receives the last check's sums.  Synchronises with the
+   stream once per check when residual_tol > 0, else once at the end.
+   Errors: LBM_EUNSTABLE when a check saw NaN/Inf (the state is left as it
+   is); LBM_ECUDA. */
+LBM_API int lbm_vanse_step(lbm_vanse_t h, long long max_steps, double residual_tol, int check_every,
+                   lbm_vanse_stats *out);
+
+/* Macroscopic fields at the current time n from the pre-collision state:
+   rho~ (eq. (density)), p = c_s^2 (rho~ - rho0), u (eq. (velocity)).
+   rho, p: N values; u: 3*N values; any may be NULL.  Solid cells get 0. */
+LBM_API int lbm_vanse_moments(lbm_vanse_t h, float *rho, float *p, float *u, int on_device);
+LBM_API int lbm_vanse_moments_f64(lbm_vanse_t h, double *rho, double *p, double *u, int on_device);
+
+/* Decoded populations f_i(x, n) in double, natural (not AA-swapped) order,
+   array of structures f[cell*Q + i]; host memory.  For checks and dumps. */
+LBM_API int lbm_vanse_get_populations(lbm_vanse_t h, double *f_host);
+
+/* Number of kernels this library has launched in this process so far (a
+   replayed graph counts each of its kernel nodes).  Diagnostic. */
+LBM_API long long lbm_vanse_launch_count(void);
+
+/* Iteration limit of the row-staged kernel's waits for its staged rows
+   (0 = the default of 2^22 polls).  A wait that runs out makes the step
+   return LBM_ETIMEOUT after the kernel has drained its copies; the state of
+   that step is then incomplete.  For testing the timeout path. */
+LBM_API int lbm_vanse_set_wait_limit(lbm_vanse_t h, unsigned spins);
+
+/* 1 if the handle's step runs the row-staged kernel, 0 for the one-cell-per-
+   thread kernel, -1 for a NULL handle. */
+LBM_API int lbm_vanse_uses_row_kernel(lbm_vanse_t h);
+
+/* Time counter n and lattice description. */
+LBM_API long long lbm_vanse_steps_done(lbm_vanse_t h);
+LBM_API int lbm_vanse_get_params(lbm_vanse_t h, lbm_vanse_params *out);
+
+/* Checkpoint: raw device state (populations in storage format, time counter,
+   parity, phi, d_t phi, force fields, shift) to a host buffer.  Call with
+   buf = NULL to get the size in *size.  Restoring into a handle created with
+   the same parameters continues bit-identically. */
+LBM_API int lbm_vanse_save_state(lbm_vanse_t h, void *buf, size_t *size);
+LBM_API int lbm_vanse_load_state(lbm_vanse_t h, const void *buf, size_t size);
+
+/* ---------------------------------------------------------------------- */
+/* Batched stepping (many independent lattices advanced by persistent,    */
+/* graph-captured kernels over one device work table of tiles).  Not in   */
+/* the paper: the paper's Sec. 2.2 update is applied to each member.      */
+/* ---------------------------------------------------------------------- */
+
+/* Create an empty batch on `stream` (cudaStream_t or NULL) holding at most
+   max_members lattices and max_tiles tiles; tile_cells is the number of
+   cells one tile covers (0 = library default).  Members must use FP32 or
+   FP16 storage. */
+LBM_API int lbm_vanse_batch_create(int max_members, int max_tiles, int tile_cells, void *stream,
+                           lbm_vanse_batch_t *out);
+LBM_API void lbm_vanse_batch_destroy(lbm_vanse_batch_t b);
+
+/* Add lattice h with a budget of max_steps further steps; the handle stays
+   owned by the caller and must outlive its membership.  Returns the member
+   slot (>= 0) or an error (LBM_ENOMEM when the table is full). */
+LBM_API int lbm_vanse_batch_add(lbm_vanse_batch_t b, lbm_vanse_t h, long long max_steps);
+LBM_API int lbm_vanse_batch_remove(lbm_vanse_batch_t b, lbm_vanse_t h);
+
+/* Advance every member by min(k, its remaining budget) steps in one graph
+   replay of k fused steps per lattice type (k even).  With check = 1 the
+   last step of the replay also reduces each member's statistics (read them
+   with lbm_vanse_batch_stats after the call; the call synchronises).
+   A member whose budget is spent idles. */
+LBM_API int lbm_vanse_batch_step(lbm_vanse_batch_t b, int k, int check);
+LBM_API int lbm_vanse_batch_stats(lbm_vanse_batch_t b, lbm_vanse_t h, lbm_vanse_stats *out);
+LBM_API int lbm_vanse_batch_size(lbm_vanse_batch_t b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_VANSE_H */

@@ -1,0 +1,155 @@
+// aux.cu -- launch geometry, step dispatch and small helper kernels.
+#include <atomic>
+
+#include <cuda_runtime.h>
+
+#include "../../include/lbm_vanse.h"
+#include "internal.h"
+
+namespace lbm {
+
+cudaError_t launch_step_fast_d2q9(const LatticeDev *, int, bool, int, int, const StepLaunch &, cudaStream_t);
+cudaError_t launch_step_fast_d3q19(const LatticeDev *, int, bool, int, int, const StepLaunch &, cudaStream_t);
+cudaError_t launch_step_fast_d3q27(const LatticeDev *, int, bool, int, int, const StepLaunch &, cudaStream_t);
+cudaError_t launch_step_exact(int lattice, const LatticeDev *L_dev, bool odd, int red, int k,
+                              const StepLaunch &ls, cudaStream_t s);
+cudaError_t launch_step_row_d2q9(const LatticeDev *, int, bool, int, int, const StepLaunch &, cudaStream_t);
+cudaError_t launch_step_row_d3q19(const LatticeDev *, int, bool, int, int, const StepLaunch &, cudaStream_t);
+cudaError_t launch_step_row_d3q27(const LatticeDev *, int, bool, int, int, const StepLaunch &, cudaStream_t);
+int plan_row_d2q9(int, int, int, int, unsigned, StepLaunch &);
+int plan_row_d3q19(int, int, int, int, unsigned, StepLaunch &);
+int plan_row_d3q27(int, int, int, int, unsigned, StepLaunch &);
+
+int plan_row_kernel(int lattice, int storage, int nx, int ny, int nz, unsigned walls, StepLaunch &ls) {
+  ls.row = 0;
+  if (storage == 0) return 0;
+  switch (lattice) {
+    case 0: return plan_row_d2q9(storage, nx, ny, nz, walls, ls);
+    case 1: return plan_row_d3q19(storage, nx, ny, nz, walls, ls);
+    case 2: return plan_row_d3q27(storage, nx, ny, nz, walls, ls);
+  }
+  return 0;
+}
+
+static int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+StepLaunch make_launch(int nx, int ny, int nz, int bx, int by) {
+  StepLaunch ls;
+  if (bx <= 0 || by <= 0) {
+    bx = round_up(nx, 32);
+    if (bx > 256) bx = 256;
+    by = 256 / bx;
+    if (by > ny) by = ny;
+    if (by < 1) by = 1;
+  }
+  ls.block = dim3(bx, by, 1);
+  ls.grid = dim3((nx + bx - 1) / bx, (ny + by - 1) / by, nz);
+  ls.block_threads = bx * by;
+  ls.row = 0;
+  ls.row_grid = 0;
+  ls.row_smem_even = ls.row_smem_odd = 0;
+  return ls;
+}
+
+cudaError_t launch_step(const LatticeDev &h, const LatticeDev *L_dev, long long n_host, int k, int red,
+                        const StepLaunch &ls, cudaStream_t s) {
+  const bool odd = ((n_host + k) & 1) != 0;
+  if (h.storage == 0) return launch_step_exact(h.lattice, L_dev, odd, red, k, ls, s);
+  if (ls.row) {
+    switch (h.lattice) {
+      case 0: return launch_step_row_d2q9(L_dev, h.storage, odd, red, k, ls, s);
+      case 1: return launch_step_row_d3q19(L_dev, h.storage, odd, red, k, ls, s);
+      case 2: return launch_step_row_d3q27(L_dev, h.storage, odd, red, k, ls, s);
+    }
+    return cudaErrorInvalidValue;
+  }
+  switch (h.lattice) {
+    case 0: return launch_step_fast_d2q9(L_dev, h.storage, odd, red, k, ls, s);
+    case 1: return launch_step_fast_d3q19(L_dev, h.storage, odd, red, k, ls, s);
+    case 2: return launch_step_fast_d3q27(L_dev, h.storage, odd, red, k, ls, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// After a chunk of k steps: advance the time counter and commit a pending
+// change of shift (the first step of the chunk re-encoded every slot).
+__global__ void advance_kernel(LatticeDev *L, int k) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    L->n += k;
+    L->sig_rd = L->sig_wr;
+  }
+}
+
+cudaError_t launch_advance(LatticeDev *L_dev, int k, cudaStream_t s) {
+  advance_kernel<<<1, 32, 0, s>>>(L_dev, k);
+  return cudaGetLastError();
+}
+
+// Deterministic sum of per-block partials: thread t adds blocks t, t+T, ...
+// in order, then a fixed tree over the threads.
+__global__ void finalize_kernel(const double *partials, int nblocks, double *out) {
+  __shared__ double sm[256][kRedWidth];
+  const int t = threadIdx.x;
+  double acc[kRedWidth];
+  for (int j = 0; j < kRedWidth; ++j) acc[j] = 0.0;
+  for (int b = t; b < nblocks; b += blockDim.x)
+    for (int j = 0; j < kRedWidth; ++j) acc[j] += partials[(long long)b * kRedWidth + j];
+  for (int j = 0; j < kRedWidth; ++j) sm[t][j] = acc[j];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (t < w)
+      for (int j = 0; j < kRedWidth; ++j) sm[t][j] += sm[t + w][j];
+    __syncthreads();
+  }
+  if (t < kRedWidth) out[t] = sm[0][t];
+}
+
+cudaError_t launch_finalize(const double *partials, int nblocks, double *out, cudaStream_t s) {
+  finalize_kernel<<<1, 256, 0, s>>>(partials, nblocks, out);
+  return cudaGetLastError();
+}
+
+__global__ void f2d_kernel(const float *in, double *out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = (double)in[i];
+}
+
+__global__ void d2f_kernel(const double *in, float *out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
+static int grid_for(long long n) {
+  long long g = (n + 255) / 256;
+  const long long cap = 152LL * 32;
+  return (int)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+cudaError_t launch_convert_f2d(const float *in, double *out, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  f2d_kernel<<<grid_for(n), 256, 0, s>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert_d2f(const double *in, float *out, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  d2f_kernel<<<grid_for(n), 256, 0, s>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+static std::atomic<long long> g_launches{0};
+
+void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+  return n > 0 ? n : 1;
+}
+
+}  // namespace lbm
+
+extern "C" long long lbm_vanse_launch_count(void) { return lbm::g_launches.load(); }

@@ -1,0 +1,434 @@
+// batch.cu -- many independent lattices advanced by persistent,
+// graph-captured kernels over one device work table.
+//
+// The table lists tiles (member, first cell, cell count) grouped by
+// (lattice, storage) type.  For each type present, one persistent kernel of
+// (SM count x resident blocks) blocks strides over that type's tiles and
+// applies the fused step of step_fast.cuh to each cell; each member keeps
+// its own descriptor (time counter, parity, phi, force), so members of any
+// size, parity and age share one launch.  A replay of k steps is a CUDA
+// graph of k launches per type plus one advance kernel; the tables live in
+// device memory, so members can join and leave (continuous batching)
+// without re-capturing the graph.
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/lbm_vanse.h"
+#include "internal.h"
+#include "step_fast.cuh"
+
+namespace lbm {
+LatticeDev *handle_device_desc(lbm_vanse_t h);
+const LatticeDev &handle_mirror(lbm_vanse_t h);
+LatticeDev &handle_mirror_mut(lbm_vanse_t h);
+int handle_push(lbm_vanse_t h);
+cudaStream_t handle_stream(lbm_vanse_t h);
+void set_global_error(const char *msg);
+}  // namespace lbm
+
+using namespace lbm;
+
+namespace {
+
+constexpr int kTypes = 6;  // (lattice 0..2) x (storage fp32, fp16)
+constexpr int kBatchBlock = 256;
+
+int type_of(int lattice, int storage) { return lattice * 2 + (storage == 2 ? 1 : 0); }
+
+// Per-type tile ranges [begin, count] live at type_range[2*type].
+struct BatchRange {
+  int begin, count;
+};
+
+template <class LAT, class ST, bool RED>
+__global__ void __launch_bounds__(kBatchBlock) batch_step_kernel(const BatchMember *__restrict__ members,
+                                                                 const BatchTile *__restrict__ tiles,
+                                                                 const BatchRange *__restrict__ range,
+                                                                 int k, int kmax, double *tile_partials) {
+  const int begin = range->begin, count = range->count;
+  for (int t = blockIdx.x; t < count; t += gridDim.x) {
+    const BatchTile tile = tiles[begin + t];
+    const BatchMember &M = members[tile.member];
+    const long long budget = M.budget;
+    if (k >= budget) continue;  // member finished inside this replay
+    const LatticeDev &L = *M.L;
+    const long long n = L.n + k;
+    const long long last = (budget < kmax ? budget : kmax) - 1;
+    const bool red_here = RED && k == last;
+    const int nx = L.nx, ny = L.ny;
+    const int c_end = tile.y0 + tile.ny;  // y0 = first cell, ny = cell count (linear tile)
+    RedAcc acc;
+#pragma unroll
+    for (int j = 0; j < kRedWidth; ++j) acc.v[j] = 0.0;
+    for (int c = tile.y0 + threadIdx.x; c < c_end; c += blockDim.x) {
+      const int x = c % nx;
+      const int r = c / nx;
+      const int y = r % ny;
+      const int z = r / ny;
+      if (red_here) {
+        if (n & 1) update_cell_fast<LAT, ST, true, true>(L, n, x, y, z, acc);
+        else update_cell_fast<LAT, ST, false, true>(L, n, x, y, z, acc);
+      } else {
+        if (n & 1) update_cell_fast<LAT, ST, true, false>(L, n, x, y, z, acc);
+        else update_cell_fast<LAT, ST, false, false>(L, n, x, y, z, acc);
+      }
+    }
+    if (red_here) {
+      block_reduce_store(acc, tile_partials, begin + t);
+      __syncthreads();
+    }
+  }
+}
+
+// After a replay of k steps: every member advances by min(k, budget).
+__global__ void batch_advance_kernel(BatchMember *members, const int *nmembers, int k) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= *nmembers) return;
+  BatchMember &M = members[m];
+  const long long s = M.budget < k ? M.budget : k;
+  if (s <= 0) return;
+  M.L->n += s;
+  M.L->sig_rd = M.L->sig_wr;
+  M.budget -= s;
+}
+
+// Per-member sums of its tiles' partials, in tile order.
+__global__ void batch_finalize_kernel(const BatchMember *members, const int *nmembers,
+                                      const double *tile_partials, double *out) {
+  const int m = blockIdx.x;
+  if (m >= *nmembers) return;
+  const int j = threadIdx.x;
+  if (j >= kRedWidth) return;
+  const BatchMember &M = members[m];
+  double s = 0.0;
+  for (int t = M.tile_begin; t < M.tile_end; ++t) s += tile_partials[(long long)t * kRedWidth + j];
+  out[(long long)m * kRedWidth + j] = s;
+}
+
+template <class LAT, class ST>
+cudaError_t launch_type(const BatchMember *members, const BatchTile *tiles, const BatchRange *range,
+                        int k, int kmax, int red, double *partials, int grid, cudaStream_t s) {
+  if (red)
+    batch_step_kernel<LAT, ST, true><<<grid, kBatchBlock, 0, s>>>(members, tiles, range, k, kmax, partials);
+  else
+    batch_step_kernel<LAT, ST, false><<<grid, kBatchBlock, 0, s>>>(members, tiles, range, k, kmax, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_type(int type, const BatchMember *members, const BatchTile *tiles,
+                              const BatchRange *range, int k, int kmax, int red, double *partials,
+                              int grid, cudaStream_t s) {
+  switch (type) {
+    case 0: return launch_type<D2Q9, float>(members, tiles, range, k, kmax, red, partials, grid, s);
+    case 1: return launch_type<D2Q9, __half>(members, tiles, range, k, kmax, red, partials, grid, s);
+    case 2: return launch_type<D3Q19, float>(members, tiles, range, k, kmax, red, partials, grid, s);
+    case 3: return launch_type<D3Q19, __half>(members, tiles, range, k, kmax, red, partials, grid, s);
+    case 4: return launch_type<D3Q27, float>(members, tiles, range, k, kmax, red, partials, grid, s);
+    case 5: return launch_type<D3Q27, __half>(members, tiles, range, k, kmax, red, partials, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+struct HostMember {
+  lbm_vanse_t h;
+  long long budget;
+  int type;
+  long long last_check_n;
+  bool have_prev;
+  double stats[kRedWidth];
+  long long stats_n;
+  long long check_k;
+};
+
+struct lbm_vanse_batch {
+  cudaStream_t stream = nullptr;
+  int max_members = 0, max_tiles = 0, tile_cells = 0;
+  std::vector<HostMember> members;
+  BatchMember *members_dev = nullptr;
+  BatchTile *tiles_dev = nullptr;
+  BatchRange *ranges_dev = nullptr;  // kTypes entries
+  int *nmembers_dev = nullptr;
+  double *tile_partials = nullptr;
+  double *out_dev = nullptr;
+  double *out_host = nullptr;
+  bool dirty = true;
+  int ntiles = 0;
+  int grid = 0;
+  std::map<std::pair<unsigned, long long>, cudaGraphExec_t> graphs;  // (types mask, k*2+red)
+  std::vector<BatchMember> members_host;
+  std::vector<BatchTile> tiles_host;
+  std::vector<BatchRange> ranges_host;
+};
+
+static int bfail(int code, const char *msg) {
+  set_global_error(msg);
+  return code;
+}
+
+extern "C" int lbm_vanse_batch_create(int max_members, int max_tiles, int tile_cells, void *stream,
+                                      lbm_vanse_batch_t *out) {
+  if (!out) return bfail(LBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (max_members < 1 || max_tiles < 1) return bfail(LBM_EINVAL, "max_members and max_tiles must be >= 1");
+  if (tile_cells < 0) return bfail(LBM_EINVAL, "tile_cells must be >= 0");
+  lbm_vanse_batch_t b = new lbm_vanse_batch();
+  b->stream = static_cast<cudaStream_t>(stream);
+  b->max_members = max_members;
+  b->max_tiles = max_tiles;
+  b->tile_cells = tile_cells > 0 ? tile_cells : 4096;
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_step_kernel<D3Q19, __half, false>, kBatchBlock, 0);
+  if (occ < 1) occ = 1;
+  b->grid = sm_count() * occ;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMalloc(&b->members_dev, sizeof(BatchMember) * max_members);
+  if (e == cudaSuccess) e = cudaMalloc(&b->tiles_dev, sizeof(BatchTile) * max_tiles);
+  if (e == cudaSuccess) e = cudaMalloc(&b->ranges_dev, sizeof(BatchRange) * kTypes);
+  if (e == cudaSuccess) e = cudaMalloc(&b->nmembers_dev, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&b->tile_partials, sizeof(double) * kRedWidth * max_tiles);
+  if (e == cudaSuccess) e = cudaMalloc(&b->out_dev, sizeof(double) * kRedWidth * max_members);
+  if (e == cudaSuccess) e = cudaMallocHost(&b->out_host, sizeof(double) * kRedWidth * max_members);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    lbm_vanse_batch_destroy(b);
+    return bfail(LBM_ENOMEM, "batch table allocation failed");
+  }
+  *out = b;
+  return LBM_OK;
+}
+
+extern "C" void lbm_vanse_batch_destroy(lbm_vanse_batch_t b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  else cudaDeviceSynchronize();
+  for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  cudaFree(b->members_dev);
+  cudaFree(b->tiles_dev);
+  cudaFree(b->ranges_dev);
+  cudaFree(b->nmembers_dev);
+  cudaFree(b->tile_partials);
+  cudaFree(b->out_dev);
+  if (b->out_host) cudaFreeHost(b->out_host);
+  delete b;
+}
+
+static int tiles_needed(const lbm_vanse_batch *b, long long ncell) {
+  return (int)((ncell + b->tile_cells - 1) / b->tile_cells);
+}
+
+extern "C" int lbm_vanse_batch_add(lbm_vanse_batch_t b, lbm_vanse_t h, long long max_steps) {
+  if (!b || !h) return bfail(LBM_EINVAL, "NULL argument");
+  if (max_steps < 0) return bfail(LBM_EINVAL, "max_steps must be >= 0");
+  const LatticeDev &m = handle_mirror(h);
+  if (m.storage == 0) return bfail(LBM_EINVAL, "batch members must use FP32 or FP16 storage");
+  for (auto &hm : b->members)
+    if (hm.h == h) return bfail(LBM_EINVAL, "lattice is already a member");
+  if ((int)b->members.size() >= b->max_members) return bfail(LBM_ENOMEM, "batch member table is full");
+  int used = 0;
+  for (auto &hm : b->members) used += tiles_needed(b, handle_mirror(hm.h).ncell);
+  if (used + tiles_needed(b, m.ncell) > b->max_tiles) return bfail(LBM_ENOMEM, "batch tile table is full");
+  // residual tracking needs the previous check's velocity
+  LatticeDev &mm = handle_mirror_mut(h);
+  if (!mm.u_prev) {
+    void *p = nullptr;
+    if (cudaMallocAsync(&p, (size_t)3 * mm.ncell * sizeof(float), handle_stream(h)) != cudaSuccess) {
+      cudaGetLastError();
+      return bfail(LBM_ENOMEM, "residual buffer allocation failed");
+    }
+    mm.u_prev = static_cast<float *>(p);
+  }
+  HostMember hm;
+  memset(&hm, 0, sizeof(hm));
+  hm.h = h;
+  hm.budget = max_steps;
+  hm.type = type_of(m.lattice, m.storage);
+  hm.last_check_n = -1;
+  hm.stats_n = -1;
+  b->members.push_back(hm);
+  b->dirty = true;
+  return (int)b->members.size() - 1;
+}
+
+extern "C" int lbm_vanse_batch_remove(lbm_vanse_batch_t b, lbm_vanse_t h) {
+  if (!b || !h) return bfail(LBM_EINVAL, "NULL argument");
+  for (size_t i = 0; i < b->members.size(); ++i)
+    if (b->members[i].h == h) {
+      b->members.erase(b->members.begin() + i);
+      b->dirty = true;
+      return LBM_OK;
+    }
+  return bfail(LBM_EINVAL, "lattice is not a member");
+}
+
+extern "C" int lbm_vanse_batch_size(lbm_vanse_batch_t b) { return b ? (int)b->members.size() : 0; }
+
+// Rebuild and upload the member and tile tables (sorted by type).
+static int upload_tables(lbm_vanse_batch_t b) {
+  const int nm = (int)b->members.size();
+  b->members_host.assign(nm, BatchMember());
+  b->tiles_host.clear();
+  b->ranges_host.assign(kTypes, BatchRange{0, 0});
+  for (int t = 0; t < kTypes; ++t) {
+    b->ranges_host[t].begin = (int)b->tiles_host.size();
+    for (int i = 0; i < nm; ++i) {
+      HostMember &hm = b->members[i];
+      if (hm.type != t) continue;
+      const LatticeDev &m = handle_mirror(hm.h);
+      BatchMember &bm = b->members_host[i];
+      bm.L = handle_device_desc(hm.h);
+      bm.budget = hm.budget;
+      bm.lattice = m.lattice;
+      bm.storage = m.storage;
+      bm.tile_begin = (int)b->tiles_host.size();
+      for (long long c = 0; c < m.ncell; c += b->tile_cells) {
+        BatchTile tl;
+        tl.member = i;
+        tl.z = 0;
+        tl.y0 = (int)c;
+        tl.ny = (int)((m.ncell - c) < b->tile_cells ? (m.ncell - c) : b->tile_cells);
+        tl.x0 = 0;
+        tl.nxt = 0;
+        b->tiles_host.push_back(tl);
+      }
+      bm.tile_end = (int)b->tiles_host.size();
+    }
+    b->ranges_host[t].count = (int)b->tiles_host.size() - b->ranges_host[t].begin;
+  }
+  b->ntiles = (int)b->tiles_host.size();
+  cudaStream_t s = b->stream;
+  cudaError_t e = cudaSuccess;
+  if (nm) e = cudaMemcpyAsync(b->members_dev, b->members_host.data(), sizeof(BatchMember) * nm, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && b->ntiles)
+    e = cudaMemcpyAsync(b->tiles_dev, b->tiles_host.data(), sizeof(BatchTile) * b->ntiles, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->ranges_dev, b->ranges_host.data(), sizeof(BatchRange) * kTypes, cudaMemcpyHostToDevice, s);
+  static thread_local int nm_host;
+  nm_host = nm;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->nmembers_dev, &nm_host, sizeof(int), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return bfail(LBM_ECUDA, cudaGetErrorString(e));
+  b->dirty = false;
+  return LBM_OK;
+}
+
+static int batch_graph(lbm_vanse_batch_t b, unsigned types, int k, int red, cudaGraphExec_t *out) {
+  auto key = std::make_pair(types, (long long)k * 2 + red);
+  auto it = b->graphs.find(key);
+  if (it != b->graphs.end()) {
+    *out = it->second;
+    return LBM_OK;
+  }
+  cudaStream_t cs;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return bfail(LBM_ECUDA, "stream create");
+  cudaGraph_t g;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    for (int j = 0; j < k && e == cudaSuccess; ++j)
+      for (int t = 0; t < kTypes && e == cudaSuccess; ++t)
+        if (types & (1u << t))
+          e = launch_batch_type(t, b->members_dev, b->tiles_dev, b->ranges_dev + t, j, k, red,
+                                b->tile_partials, b->grid, cs);
+    if (e == cudaSuccess) {
+      batch_advance_kernel<<<(b->max_members + 127) / 128, 128, 0, cs>>>(b->members_dev, b->nmembers_dev, k);
+      e = cudaGetLastError();
+    }
+    if (red && e == cudaSuccess) {
+      batch_finalize_kernel<<<b->max_members, 32, 0, cs>>>(b->members_dev, b->nmembers_dev, b->tile_partials, b->out_dev);
+      e = cudaGetLastError();
+    }
+    cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) {
+    cudaGraphExec_t ge;
+    e = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    if (e == cudaSuccess) {
+      b->graphs[key] = ge;
+      *out = ge;
+    }
+  }
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) return bfail(LBM_ECUDA, cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+extern "C" int lbm_vanse_batch_step(lbm_vanse_batch_t b, int k, int check) {
+  if (!b) return bfail(LBM_EINVAL, "batch is NULL");
+  if (k < 1) return bfail(LBM_EINVAL, "k must be >= 1");
+  if (b->members.empty()) return LBM_OK;
+  int rc;
+  // members' descriptors must be current on the device (their own streams
+  // may have pending uploads): synchronise those streams first
+  unsigned types = 0;
+  for (auto &hm : b->members) {
+    LatticeDev &m = handle_mirror_mut(hm.h);
+    m.have_prev = hm.have_prev ? 1 : 0;
+    if ((rc = handle_push(hm.h))) return bfail(rc, "member descriptor upload failed");
+    cudaStreamSynchronize(handle_stream(hm.h));
+    types |= 1u << hm.type;
+  }
+  if ((rc = upload_tables(b))) return rc;
+  cudaGraphExec_t ge;
+  if ((rc = batch_graph(b, types, k, check ? 1 : 0, &ge))) return rc;
+  cudaError_t e = cudaGraphLaunch(ge, b->stream);
+  if (e != cudaSuccess) return bfail(LBM_ECUDA, cudaGetErrorString(e));
+  count_launches((long long)k * __builtin_popcount(types) + 1 + (check ? 1 : 0));
+  if (check) {
+    e = cudaMemcpyAsync(b->out_host, b->out_dev, sizeof(double) * kRedWidth * b->members.size(),
+                        cudaMemcpyDeviceToHost, b->stream);
+    if (e != cudaSuccess) return bfail(LBM_ECUDA, cudaGetErrorString(e));
+  }
+  e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bfail(LBM_ECUDA, cudaGetErrorString(e));
+  // host mirrors follow the device
+  for (size_t i = 0; i < b->members.size(); ++i) {
+    HostMember &hm = b->members[i];
+    const long long s = hm.budget < k ? hm.budget : k;
+    if (s <= 0) continue;
+    LatticeDev &m = handle_mirror_mut(hm.h);
+    const long long n_check = m.n + s - 1;
+    m.n += s;
+    m.sig_rd = m.sig_wr;
+    hm.budget -= s;
+    if (check) {
+      memcpy(hm.stats, b->out_host + i * kRedWidth, sizeof(hm.stats));
+      hm.check_k = hm.last_check_n >= 0 ? n_check - hm.last_check_n : 0;
+      hm.stats_n = n_check;
+      hm.last_check_n = n_check;
+      hm.have_prev = true;
+    }
+  }
+  return LBM_OK;
+}
+
+extern "C" int lbm_vanse_batch_stats(lbm_vanse_batch_t b, lbm_vanse_t h, lbm_vanse_stats *out) {
+  if (!b || !h || !out) return bfail(LBM_EINVAL, "NULL argument");
+  for (auto &hm : b->members)
+    if (hm.h == h) {
+      memset(out, 0, sizeof(*out));
+      const double *s = hm.stats;
+      out->mass = s[0];
+      out->momentum[0] = s[1];
+      out->momentum[1] = s[2];
+      out->momentum[2] = s[3];
+      out->u_norm = std::sqrt(s[5]);
+      out->force[0] = s[7];
+      out->force[1] = s[8];
+      out->force[2] = s[9];
+      out->residual = (hm.check_k > 0 && s[5] > 0.0) ? std::sqrt(s[4]) / (hm.check_k * std::sqrt(s[5])) : -1.0;
+      out->steps_done = handle_mirror(h).n;
+      out->step_of_stats = hm.stats_n;
+      out->nan_seen = s[6] > 0.0 || !std::isfinite(s[0]) || !std::isfinite(s[5]);
+      out->converged = 0;
+      return LBM_OK;
+    }
+  return bfail(LBM_EINVAL, "lattice is not a member");
+}

@@ -1,0 +1,49 @@
+// step_fast_d3q19.cu -- D3Q19 instantiations of the fused FP32/FP16 step.
+#include "step_fast.cuh"
+
+namespace lbm {
+
+cudaError_t launch_step_fast_d3q19(const LatticeDev *L_dev, int storage, bool odd, int red, int k,
+                                   const StepLaunch &ls, cudaStream_t s) {
+  if (storage == 1) {
+    if (odd) {
+      if (red) step_fast_kernel<D3Q19, float, true, true><<<ls.grid, ls.block, 0, s>>>(L_dev, k);
+      else step_fast_kernel<D3Q19, float, true, false><<<ls.grid, ls.block, 0, s>>>(L_dev, k);
+    } else {
+      if (red) step_fast_kernel<D3Q19, float, false, true><<<ls.grid, ls.block, 0, s>>>(L_dev, k);
+      else step_fast_kernel<D3Q19, float, false, false><<<ls.grid, ls.block, 0, s>>>(L_dev, k);
+    }
+  } else if (storage == 2) {
+    if (odd) {
+      if (red) step_fast_kernel<D3Q19, __half, true, true><<<ls.grid, ls.block, 0, s>>>(L_dev, k);
+      else step_fast_kernel<D3Q19, __half, true, false><<<ls.grid, ls.block, 0, s>>>(L_dev, k);
+    } else {
+      if (red) step_fast_kernel<D3Q19, __half, false, true><<<ls.grid, ls.block, 0, s>>>(L_dev, k);
+      else step_fast_kernel<D3Q19, __half, false, false><<<ls.grid, ls.block, 0, s>>>(L_dev, k);
+    }
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace lbm
+
+#include "step_row.cuh"
+
+namespace lbm {
+
+cudaError_t launch_step_row_d3q19(const LatticeDev *L_dev, int storage, bool odd, int red, int k,
+                                  const StepLaunch &ls, cudaStream_t s) {
+  if (storage == 1) return launch_row_t<D3Q19, float, 3>(L_dev, odd, red, k, ls, s);
+  if (storage == 2) return launch_row_t<D3Q19, __half, 3>(L_dev, odd, red, k, ls, s);
+  return cudaErrorInvalidValue;
+}
+
+int plan_row_d3q19(int storage, int nx, int ny, int nz, unsigned walls, StepLaunch &ls) {
+  if (storage == 1) return plan_row_t<D3Q19, float, 3>(nx, ny, nz, walls, ls);
+  if (storage == 2) return plan_row_t<D3Q19, __half, 3>(nx, ny, nz, walls, ls);
+  return 0;
+}
+
+}  // namespace lbm

@@ -121,8 +121,11 @@ def eps_random_spheres(shape, seed_offset: int = 3, rmin: float = 4.0, rmax: flo
     y = np.arange(ny)
     z = np.arange(nz)
     count = 0
+    flat = nz == 1          # a 2D lattice: the spheres become disks in z = 0
     while solid < packing * ntot and count < max_spheres:
         c = g.uniform(0, 1, 3) * np.array([nx, ny, nz])
+        if flat:
+            c[2] = 0.0
         r = g.uniform(rmin, rmax)
         count += 1
         # bounding box (periodic on every axis except the wall axis)
@@ -131,6 +134,11 @@ def eps_random_spheres(shape, seed_offset: int = 3, rmin: float = 4.0, rmax: flo
             lo, hi = int(math.floor(cc - r)), int(math.ceil(cc + r)) + 1
             idx = np.arange(lo, hi)
             axis_id = {0: 2, 1: 1, 2: 0}[ax]          # (z,y,x) -> lattice axis id
+            if ax == 0 and flat:
+                idx = np.array([0])
+            # a box wider than the lattice would repeat indices in the scatter
+            if len(idx) > ax_len:
+                idx = idx[:ax_len]
             if wall_axis is not None and axis_id == wall_axis:
                 idx = idx[(idx >= 0) & (idx < ax_len)]
             sl.append(idx)

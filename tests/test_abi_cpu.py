@@ -1,0 +1,68 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds for
+sm_103a, loads, and exports every entry point the public header declares;
+the Python binding wraps each of them."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from conftest import ROOT
+from paper_2208_09267_gb300 import build, lbm
+
+HEADER = os.path.join(ROOT, "include", "lbm_vanse.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^LBM_API[^;(]*?\b(lbm_vanse_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_the_abi():
+    names = declared_functions()
+    for required in ("lbm_vanse_create", "lbm_vanse_set_epsilon", "lbm_vanse_set_force",
+                     "lbm_vanse_step", "lbm_vanse_moments", "lbm_vanse_destroy"):
+        assert required in names
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    path = build.build()
+    assert os.path.exists(path)
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\bT (lbm_vanse_\w+)", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+
+
+def test_library_loads_and_binding_covers_the_header():
+    L = lbm.lib()
+    for name in declared_functions():
+        assert hasattr(L, name)
+        assert name in lbm._SIGS, f"binding lacks {name}"
+    assert set(lbm._SIGS) == set(declared_functions())
+    assert "sm_103a" in lbm.version()
+
+
+def test_struct_layouts_match_the_header():
+    """The binding's ctypes structs have the header's field order and size."""
+    text = open(HEADER).read()
+    body = text[text.index("typedef struct {", text.index("LBM_AXIS_X")):text.index("} lbm_vanse_params;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"\b(\w+)(?:\s*,\s*(\w+))?(?:\s*,\s*(\w+))?\s*;", body)
+    flat = [f for group in fields for f in group if f]
+    assert [f[0] for f in lbm.Params._fields_] == flat
+    assert ctypes.sizeof(lbm.Params) == 88
+
+
+def test_params_default_and_device_bytes_need_no_gpu():
+    p = lbm.Params()
+    assert lbm.lib().lbm_vanse_params_default(ctypes.byref(p)) == 0
+    assert (p.lattice, p.storage, p.nx, p.tau) == (1, 1, 32, 0.6)
+    b32 = lbm.device_bytes("D3Q19", (256, 256, 256), "fp32")
+    b16 = lbm.device_bytes("D3Q19", (256, 256, 256), "fp16")
+    n = 256 ** 3
+    assert 19 * n * 4 < b32 < 19 * n * 4 + 3 * n * 4 + (1 << 24)
+    assert 19 * n * 2 < b16 < b32
+    assert lbm.device_bytes("D2Q9", (4, 4, 2)) == 0  # invalid: D2Q9 needs nz = 1

@@ -1,0 +1,327 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+* FP64 storage follows the canonical evaluation order: populations and
+  moments must be bit-identical to the oracle's.
+* FP32 storage: relative L2 error of u and p <= 1e-5 after the stated steps.
+* FP16-shifted storage: relative L2 error of u and p <= 2e-3.
+Both sides receive the same seeded inputs (reduced-precision storages get
+phi and forces rounded to float32 first, and so does the oracle).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2208_09267_gb300 import inputs as I
+from paper_2208_09267_gb300 import lbm
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-5, "fp16": 2e-3}
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def make_pair(lattice, shape_xyz, storage, tau, eps, deps=None, n_eps=0, g=(0, 0, 0), force=None,
+              dforce=None, n_force=0, walls=0, quad_axes=0, fp16_k=10, block=(0, 0)):
+    """A GPU lattice and an oracle problem with identical inputs."""
+    nx, ny, nz = shape_xyz
+    f32 = storage != "fp64"
+
+    def cast(a):
+        if a is None:
+            return None
+        a = np.ascontiguousarray(a, np.float64).ravel()
+        return a.astype(np.float32).astype(np.float64) if f32 else a
+    eps, deps, force, dforce = cast(eps), cast(deps), cast(force), cast(dforce)
+    gpu = lbm.Lattice(lattice, (nx, ny, nz), tau=tau, storage=storage, walls=walls,
+                      quad_axes=quad_axes, fp16_scale_log2=fp16_k, block=block)
+    gpu.set_epsilon(eps, deps, n_eps, f64=True)
+    gpu.set_force(g, force, dforce, n_force, f64=True)
+    P = oracle.Problem(lattice, nx, ny, nz, tau=tau, walls=walls,
+                       quad_axes=quad_axes if quad_axes else None, eps_ref=eps, deps_dt=deps,
+                       n_eps=n_eps, g=g, force=force, dforce_dt=dforce, n_force=n_force)
+    return gpu, P
+
+
+def oracle_moments(P, f, n):
+    m = P.moments(f, n)
+    return m["rho"].ravel(), m["p"].ravel(), m["u"].reshape(3, -1)
+
+
+# ------------------------------------------------------------------ FP64
+
+def test_fp64_config1_bit_identical():
+    """D2Q9 64x64 periodic, FP64, tau = 0.8, phi = 0.8 + 0.1 sin sin, uniform
+    force (1e-6, 0), rest start, 1000 steps: every population and every
+    moment bit-identical to the oracle."""
+    eps = I.eps_static_sine(64)
+    gpu, P = make_pair("D2Q9", (64, 64, 1), "fp64", 0.8, eps, g=(1e-6, 0.0, 0.0))
+    gpu.init_equilibrium()
+    f = P.init()
+    st = gpu.step(1000)
+    f = P.run(f, 0, 1000)
+    assert st["steps_done"] == 1000 and gpu.steps_done == 1000
+    assert np.array_equal(gpu.populations(), f)
+    m = gpu.moments()
+    rho, p, u = oracle_moments(P, f, 1000)
+    assert np.array_equal(m["rho"], rho)
+    assert np.array_equal(m["p"], p)
+    assert np.array_equal(m["u"], u)
+    assert abs(st["mass"] - f.sum()) < 1e-12 * f.sum()
+
+
+def test_fp64_unit_volume_fraction_is_plain_bgk():
+    """phi == 1 on the GPU: the step reduces to plain BGK with Guo forcing
+    (independent numpy solver), to rounding."""
+    from plain_bgk import PlainBGK
+    gpu, P = make_pair("D2Q9", (40, 24, 1), "fp64", 0.8, np.ones(40 * 24), g=(1e-5, 2e-6, 0.0))
+    rng = np.random.default_rng(11)
+    u0 = 1e-2 * rng.standard_normal((3, 40 * 24))
+    u0[2] = 0
+    gpu.init_equilibrium(u0=u0)
+    gpu.step(60)
+    ref = PlainBGK("D2Q9", (40, 24), 0.8, (1e-5, 2e-6))
+    uu = np.stack([u0[a].reshape(24, 40).T for a in range(2)])
+    fr = ref.equilibrium(np.ones((40, 24)), uu)
+    for _ in range(60):
+        fr = ref.step(fr)
+    rho_r, u_r, _ = ref.macro(fr)
+    m = gpu.moments()
+    assert np.abs(m["u"][0].reshape(24, 40).T - u_r[0]).max() < 1e-15
+    assert np.abs(m["u"][1].reshape(24, 40).T - u_r[1]).max() < 1e-15
+
+
+@pytest.mark.parametrize("lattice", ["D2Q9", "D3Q19", "D3Q27"])
+def test_fp64_ragged_walls_timevarying_bit_identical(lattice):
+    """Ragged sizes (several blocks plus a tail), walls on y, phi with a time
+    derivative and a refresh, a per-cell force field with its derivative,
+    initial state with p0, u0 and both init modes, odd and even step counts:
+    FP64 populations stay bit-identical to the oracle."""
+    d = 2 if lattice == "D2Q9" else 3
+    shape = (45, 23, 1) if d == 2 else (37, 11, 6)
+    N = int(np.prod(shape))
+    rng = np.random.default_rng(12)
+    eps = 0.5 + 0.4 * rng.random(N)
+    deps = 1e-4 * rng.standard_normal(N)
+    force = 1e-5 * rng.standard_normal(3 * N)
+    dforce = 1e-7 * rng.standard_normal(3 * N)
+    gpu, P = make_pair(lattice, shape, "fp64", 0.66, eps, deps, 2, (1e-5, -2e-6, 3e-6), force,
+                       dforce, 1, walls=2)
+    p0 = 1e-3 * rng.standard_normal(N)
+    u0 = 1e-2 * rng.standard_normal(3 * N)
+    gpu.init_equilibrium(p0=p0, u0=u0, integral=True, half_force=True)
+    f = P.init(p0=p0, u0=u0.reshape(3, N)[:d], with_integral=True, half_force=True)
+    assert np.array_equal(gpu.populations(), f)
+    gpu.step(7)
+    f = P.run(f, 0, 7)
+    assert np.array_equal(gpu.populations(), f)
+    eps2 = np.clip(eps + 7 * deps, 0.05, 1.0)
+    deps2 = -deps
+    gpu.set_epsilon(eps2, deps2, 7, f64=True)
+    P.set_epsilon(eps2, deps2, 7)
+    gpu.step(70, check_every=9)
+    f = P.run(f, 7, 70)
+    assert gpu.steps_done == 77
+    assert np.array_equal(gpu.populations(), f)
+    m = gpu.moments()
+    rho, p, u = oracle_moments(P, f, 77)
+    assert np.array_equal(m["p"], p) and np.array_equal(m["u"], u)
+
+
+# ------------------------------------------------------- FP32 and FP16
+
+def travelling_case(L, storage, steps=300, k_eps=10, shape=None):
+    """The space-time varying D3Q19 workload (tau 0.6, force 1e-6 x), phi
+    refreshed every k_eps steps from its analytic value and derivative."""
+    shape = shape or (L, L, L)
+    nz, ny, nx = shape[2], shape[1], shape[0]
+    e0, d0 = I.eps_travelling_wave(L, 0.0, shape=(nz, ny, nx))
+    gpu, P = make_pair("D3Q19", (nx, ny, nz), storage, 0.6, e0, d0, 0, (1e-6, 0, 0))
+    gpu.init_equilibrium()
+    f = P.init()
+    n = 0
+    while n < steps:
+        k = min(k_eps, steps - n)
+        gpu.step(k)
+        f = P.run(f, n, k)
+        n += k
+        e, dd = I.eps_travelling_wave(L, float(n), shape=(nz, ny, nx))
+        e32 = e.astype(np.float32).astype(np.float64)
+        d32 = dd.astype(np.float32).astype(np.float64)
+        gpu.set_epsilon(e32, d32, n, f64=True)
+        P.set_epsilon(e32, d32, n)
+    return gpu, P, f, n
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_travelling_wave_d3q19_parity(storage):
+    gpu, P, f, n = travelling_case(40, storage, steps=300, shape=(40, 36, 34))
+    m = gpu.moments()
+    rho, p, u = oracle_moments(P, f, n)
+    eu = rel_l2(m["u"], u)
+    ep = rel_l2(m["p"] - m["p"].mean(), p - p.mean())
+    assert eu <= TOL[storage], eu
+    assert ep <= TOL[storage], ep
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+@pytest.mark.parametrize("lattice", ["D2Q9", "D3Q27"])
+def test_static_porous_walls_parity(lattice, storage):
+    """Random-sphere porous field, walls on y, body force: D2Q9 and D3Q27."""
+    d = 2 if lattice == "D2Q9" else 3
+    shape = (70, 34, 1) if d == 2 else (48, 26, 20)
+    nx, ny, nz = shape
+    eps = I.eps_random_spheres((nz, ny, nx), seed_offset=13, rmin=2, rmax=5, sigma=1.5,
+                               wall_axis=1)
+    gpu, P = make_pair(lattice, shape, storage, 0.6, eps, g=(1e-5, 0, 0), walls=2)
+    gpu.init_equilibrium()
+    f = P.init()
+    gpu.step(400)
+    f = P.run(f, 0, 400)
+    m = gpu.moments()
+    rho, p, u = oracle_moments(P, f, 400)
+    assert rel_l2(m["u"], u) <= TOL[storage]
+    assert rel_l2(m["p"] - m["p"].mean(), p - p.mean()) <= TOL[storage]
+
+
+def test_fp32_populations_track_the_oracle():
+    """Decoded FP32 populations (shift sigma = phi_ref, AA layout at odd n)
+    agree with the oracle's to float precision."""
+    gpu, P, f, n = travelling_case(24, "fp32", steps=51, k_eps=5)
+    g = gpu.populations()
+    assert np.abs(g - f).max() < 1e-6 * np.abs(f).max()
+
+
+# ------------------------------------------------------------ invariants
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+def test_checks_report_mass_and_momentum_balance(storage):
+    """Consecutive check steps on a periodic lattice: mass is constant and
+    sum J(n+1) - sum J(n) = sum F(n) (Guo momentum input)."""
+    N = 30 * 26 * 22
+    rng = np.random.default_rng(14)
+    eps = 0.6 + 0.3 * rng.random(N)
+    gpu, P = make_pair("D3Q19", (30, 26, 22), storage, 0.7, eps, g=(2e-5, 0, 1e-5))
+    gpu.init_equilibrium(integral=True, half_force=True)
+    a = gpu.step(1)
+    b = gpu.step(1)
+    tol = 1e-12 if storage == "fp64" else 1e-6
+    assert abs(b["mass"] - a["mass"]) <= tol * a["mass"]
+    # momentum reported is sum(J + F/2): difference = (F(n) + F(n+1))/2
+    for c in range(3):
+        dmom = b["momentum"][c] - a["momentum"][c]
+        expect = 0.5 * (a["force"][c] + b["force"][c])
+        assert abs(dmom - expect) <= 1e-4 * max(abs(expect), 1e-12) + tol
+
+
+def test_residual_stops_a_converging_run():
+    """A channel flow relaxes to steady state; a residual target stops the
+    run early and reports convergence."""
+    gpu = lbm.Lattice("D2Q9", (1, 34, 1), tau=0.8, storage="fp32", walls=2)
+    gpu.set_force((1e-6, 0, 0))
+    st = gpu.step(200000, residual_tol=1e-7, check_every=200)
+    assert st["converged"] and st["steps_done"] < 200000
+    assert 0 <= st["residual"] <= 1e-7
+
+
+def test_save_load_continues_bit_identically():
+    gpu, P, f, n = travelling_case(20, "fp16", steps=33, k_eps=11)
+    state = gpu.save_state()
+    gpu.step(17)
+    ref = gpu.populations()
+    other = lbm.Lattice("D3Q19", (20, 20, 20), tau=0.6, storage="fp16")
+    other.load_state(state)
+    assert other.steps_done == n
+    other.step(17)
+    assert np.array_equal(other.populations(), ref)
+
+
+def test_invalid_inputs_are_rejected():
+    gpu = lbm.Lattice("D2Q9", (8, 8, 1), storage="fp32")
+    bad = np.ones(64)
+    bad[3] = 1.5
+    with pytest.raises(lbm.LbmError) as e:
+        gpu.set_epsilon(bad)
+    assert e.value.code == -1
+    with pytest.raises(lbm.LbmError):
+        lbm.Lattice("D2Q9", (8, 8, 2))
+    with pytest.raises(lbm.LbmError):
+        lbm.Lattice("D3Q19", (8, 8, 8), tau=0.5)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.Lattice("D3Q19", (64, 64, 64), hbm_budget_bytes=1 << 20)
+    assert e.value.code == -2
+
+
+# ------------------------------------------------------- row-staged kernel
+
+def _row_pair(lattice, shape, storage, walls, tv, steps_chunks, refresh=True):
+    nx, ny, nz = shape
+    N = nx * ny * nz
+    rng = np.random.default_rng(21)
+    eps = (0.55 + 0.4 * rng.random(N)).astype(np.float32).astype(np.float64)
+    deps = (1e-4 * rng.standard_normal(N)).astype(np.float32).astype(np.float64) if tv else None
+    out = []
+    for kern in ("cell", "row"):
+        lat = lbm.Lattice(lattice, shape, tau=0.62, storage=storage, walls=walls, kernel=kern)
+        assert lat.row_kernel == (kern == "row")
+        lat.set_epsilon(eps, deps, 0, f64=True)
+        lat.set_force((2e-5, 1e-6, 0.0))
+        lat.init_equilibrium(integral=True, half_force=True)
+        n = 0
+        for j, k in enumerate(steps_chunks):
+            lat.step(k, check_every=max(1, k // 2))
+            n += k
+            if refresh and j == 0:
+                e2 = np.clip(eps + n * (deps if tv else 0), 0.05, 1.0)
+                lat.set_epsilon(e2, deps, n, f64=True)
+        out.append(lat)
+    P = oracle.Problem(lattice, nx, ny, nz, tau=0.62, walls=walls, eps_ref=eps, deps_dt=deps,
+                       g=(2e-5, 1e-6, 0.0))
+    f = P.init(with_integral=True, half_force=True)
+    n = 0
+    for j, k in enumerate(steps_chunks):
+        f = P.run(f, n, k)
+        n += k
+        if refresh and j == 0:
+            e2 = np.clip(eps + n * (deps if tv else 0), 0.05, 1.0)
+            P.set_epsilon(e2, deps, n)
+    return out, P, f, n
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+@pytest.mark.parametrize("lattice,shape,walls", [
+    ("D2Q9", (96, 40, 1), 2), ("D3Q19", (64, 20, 12), 0), ("D3Q19", (64, 18, 14), 6),
+    ("D3Q27", (64, 14, 10), 2)])
+def test_row_kernel_matches_cell_kernel_and_oracle(lattice, shape, walls, storage):
+    """The row-staged kernel (TMA bulk copies of whole rows) and the
+    one-cell-per-thread kernel compute the same update: equal populations to
+    float rounding, and both within tolerance of the oracle (time-varying
+    phi with a refresh, check steps, walls on y and z)."""
+    (cell, row), P, f, n = _row_pair(lattice, shape, storage, walls, True, [13, 24])
+    pc, pr = cell.populations(), row.populations()
+    assert np.abs(pr - pc).max() <= 4e-6 * np.abs(pc).max()
+    m = row.moments()
+    rho, p, u = oracle_moments(P, f, n)
+    assert rel_l2(m["u"], u) <= TOL[storage]
+    assert rel_l2(m["p"] - m["p"].mean(), p - p.mean()) <= TOL[storage]
+
+
+def test_row_kernel_wait_limit_reports_timeout():
+    """A stage wait that runs out ends the step with LBM_ETIMEOUT (after the
+    kernel drained its own copies); with the normal limit the handle keeps
+    working."""
+    lat = lbm.Lattice("D3Q19", (128, 64, 64), tau=0.6, storage="fp32", kernel="row")
+    lat.set_force((1e-6, 0, 0))
+    lat.set_wait_limit(1)
+    with pytest.raises(lbm.LbmError) as e:
+        for _ in range(50):
+            lat.step(2)
+    assert e.value.code == -5
+    lat.set_wait_limit(0)
+    lat.init_equilibrium()
+    st = lat.step(4)
+    assert not st["nan_seen"] and st["mass"] > 0
