@@ -211,9 +211,11 @@ LBM_API long long lbm_vanse_launch_count(void);
 
 /* Iteration limit of the row-staged kernel's waits for its staged rows
    (0 = the default of 2^22 polls).  A wait that runs out makes the step
-   return LBM_ETIMEOUT after the kernel has drained its copies; the state of
-   that step is then incomplete.  For testing the timeout path. */
-LBM_API int lbm_vanse_set_wait_limit(lbm_vanse_t h, unsigned spins);
+   return LBM_ETIMEOUT after the kernel has drained the copies it had in
+   flight; the state of that step is then incomplete.  withhold_copies = 1
+   (testing the timeout path only) makes the kernel issue no copies, so its
+   first wait runs out on a barrier that nothing completes. */
+LBM_API int lbm_vanse_set_wait_limit(lbm_vanse_t h, unsigned spins, int withhold_copies);
 
 /* 1 if the handle's step runs the row-staged kernel, 0 for the one-cell-per-
    thread kernel, -1 for a NULL handle. */

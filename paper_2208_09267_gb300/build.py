@@ -18,8 +18,11 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
-BUILD = os.path.join(HERE, "_build")
+# LBM_BUILD_DIR / LBM_NVCC_FLAGS select another build directory and extra
+# compiler flags (used to compare kernel variants side by side)
+BUILD = os.environ.get("LBM_BUILD_DIR") or os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbm_vanse.so")
+ENV_FLAGS = tuple(os.environ.get("LBM_NVCC_FLAGS", "").split())
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -66,6 +69,7 @@ def _compile(src: str, extra_flags=()) -> str:
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     """Compile every CUDA source and link the shared library; returns its path.
     Skips the work when the sources have not changed since the last build."""
+    extra_flags = tuple(extra_flags) + ENV_FLAGS
     os.makedirs(BUILD, exist_ok=True)
     stamp = os.path.join(BUILD, "stamp.txt")
     fp = _fingerprint() + repr(tuple(extra_flags))

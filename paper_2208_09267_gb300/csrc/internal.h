@@ -49,7 +49,7 @@ struct LatticeDev {
   int pad1;
   int *status;             // device flag: nonzero after a bounded wait gave up
   unsigned wait_limit;     // iteration limit of the row kernel's stage waits
-  unsigned pad2;
+  int withhold_copies;     // test only: the row kernel issues no copies
 };
 
 constexpr int kRedWidth = 12;  // M0, mom x/y/z, |du|^2, |u|^2, nan, F x/y/z, spare x2

@@ -887,10 +887,11 @@ cudaStream_t handle_stream(lbm_vanse_t h) { return h->stream; }
 void set_global_error(const char *msg) { g_last_error = msg; }
 }  // namespace lbm
 
-extern "C" int lbm_vanse_set_wait_limit(lbm_vanse_t h, unsigned spins) {
+extern "C" int lbm_vanse_set_wait_limit(lbm_vanse_t h, unsigned spins, int withhold_copies) {
   if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
   h->h.wait_limit = spins ? spins : (1u << 22);
+  h->h.withhold_copies = withhold_copies ? 1 : 0;
   return push_mirror(h);
 }
 
-extern "C" int lbm_vanse_uses_row_kernel(lbm_vanse_t h) { return h ? h->ls.row : -1; }
+extern "C" int lbm_vanse_uses_row_kernel(lbm_vanse_t h) { return h ? (h->ls.row ? 1 : 0) : -1; }

@@ -125,7 +125,7 @@ __device__ __forceinline__ void update_cell_fast(const LatticeDev &L, long long 
     } else {
       const long long m = C.at(-cx, -cy, -cz);
       d[i] = fmaf(PopIO<ST>::ld(pop + (long long)opp_of(i) * plane + m), inv_scale,
-                  rho0 * __ldg(srd + m) - s_x);
+                  fmaf(rho0, __ldg(srd + m), -s_x));
     }
   }
 
@@ -244,21 +244,23 @@ __device__ __forceinline__ void update_cell_fast(const LatticeDev &L, long long 
     const float deq = fmaf(M0, pm1, dM);
     const float src = cf * fmaf(9.0f * cu, cF, 3.0f * (cF - uF));
     const float ds = fmaf(omega, deq - d[i], d[i]) + src;
+    // the shift difference uses the exact product rho0*sigma (FMA) exactly
+    // as the decode does, so that a stored value round-trips
     if (!ODD) {
       float q = ds;
-      if (reshift) q += s_x - rho0 * __ldg(swr + cell);
+      if (reshift) q += fmaf(-rho0, __ldg(swr + cell), s_x);
       PopIO<ST>::st(pop + (long long)opp_of(i) * plane + cell, q * scale);
     } else if (i == 0) {
       float q = ds;
-      if (reshift) q += s_x - rho0 * __ldg(swr + cell);
+      if (reshift) q += fmaf(-rho0, __ldg(swr + cell), s_x);
       PopIO<ST>::st(pop + cell, q * scale);
     } else if (walls && solid_at(walls, x, y, z, cx, cy, cz, nx, ny, nz)) {
       float q = ds;
-      if (reshift) q += s_x - rho0 * __ldg(swr + cell);
+      if (reshift) q += fmaf(-rho0, __ldg(swr + cell), s_x);
       PopIO<ST>::st(pop + (long long)opp_of(i) * plane + cell, q * scale);
     } else {
       const long long m = C.at(cx, cy, cz);
-      const float q = ds + (s_x - rho0 * __ldg(swr + m));
+      const float q = ds + fmaf(-rho0, __ldg(swr + m), s_x);
       PopIO<ST>::st(pop + (long long)i * plane + m, q * scale);
     }
   }

@@ -31,18 +31,22 @@ cudaError_t launch_step_fast_d2q9(const LatticeDev *L_dev, int storage, bool odd
 
 #include "step_row.cuh"
 
+#ifndef LBM_ROW_MINB_D2Q9
+#define LBM_ROW_MINB_D2Q9 2
+#endif
+
 namespace lbm {
 
 cudaError_t launch_step_row_d2q9(const LatticeDev *L_dev, int storage, bool odd, int red, int k,
                                   const StepLaunch &ls, cudaStream_t s) {
-  if (storage == 1) return launch_row_t<D2Q9, float, 3>(L_dev, odd, red, k, ls, s);
-  if (storage == 2) return launch_row_t<D2Q9, __half, 3>(L_dev, odd, red, k, ls, s);
+  if (storage == 1) return launch_row_t<D2Q9, float, LBM_ROW_MINB_D2Q9>(L_dev, odd, red, k, ls, s);
+  if (storage == 2) return launch_row_t<D2Q9, __half, LBM_ROW_MINB_D2Q9>(L_dev, odd, red, k, ls, s);
   return cudaErrorInvalidValue;
 }
 
 int plan_row_d2q9(int storage, int nx, int ny, int nz, unsigned walls, StepLaunch &ls) {
-  if (storage == 1) return plan_row_t<D2Q9, float, 3>(nx, ny, nz, walls, ls);
-  if (storage == 2) return plan_row_t<D2Q9, __half, 3>(nx, ny, nz, walls, ls);
+  if (storage == 1) return plan_row_t<D2Q9, float, LBM_ROW_MINB_D2Q9>(nx, ny, nz, walls, ls);
+  if (storage == 2) return plan_row_t<D2Q9, __half, LBM_ROW_MINB_D2Q9>(nx, ny, nz, walls, ls);
   return 0;
 }
 

@@ -31,18 +31,22 @@ cudaError_t launch_step_fast_d3q27(const LatticeDev *L_dev, int storage, bool od
 
 #include "step_row.cuh"
 
+#ifndef LBM_ROW_MINB_D3Q27
+#define LBM_ROW_MINB_D3Q27 1
+#endif
+
 namespace lbm {
 
 cudaError_t launch_step_row_d3q27(const LatticeDev *L_dev, int storage, bool odd, int red, int k,
                                   const StepLaunch &ls, cudaStream_t s) {
-  if (storage == 1) return launch_row_t<D3Q27, float, 2>(L_dev, odd, red, k, ls, s);
-  if (storage == 2) return launch_row_t<D3Q27, __half, 2>(L_dev, odd, red, k, ls, s);
+  if (storage == 1) return launch_row_t<D3Q27, float, LBM_ROW_MINB_D3Q27>(L_dev, odd, red, k, ls, s);
+  if (storage == 2) return launch_row_t<D3Q27, __half, LBM_ROW_MINB_D3Q27>(L_dev, odd, red, k, ls, s);
   return cudaErrorInvalidValue;
 }
 
 int plan_row_d3q27(int storage, int nx, int ny, int nz, unsigned walls, StepLaunch &ls) {
-  if (storage == 1) return plan_row_t<D3Q27, float, 2>(nx, ny, nz, walls, ls);
-  if (storage == 2) return plan_row_t<D3Q27, __half, 2>(nx, ny, nz, walls, ls);
+  if (storage == 1) return plan_row_t<D3Q27, float, LBM_ROW_MINB_D3Q27>(nx, ny, nz, walls, ls);
+  if (storage == 2) return plan_row_t<D3Q27, __half, LBM_ROW_MINB_D3Q27>(nx, ny, nz, walls, ls);
   return 0;
 }
 

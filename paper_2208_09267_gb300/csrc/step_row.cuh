@@ -31,7 +31,10 @@
 
 namespace lbm {
 
-constexpr int kRowThreads = 256;
+constexpr int kConsumerWarps = 7;
+constexpr int kRowBlock = (kConsumerWarps + 1) * 32;  // + one producer warp: 8 warps, so two
+                                                      // blocks give every SM sub-partition
+                                                      // four warps and 128 registers each
 constexpr unsigned kWaitSpins = 1u << 22;  // bounded mbarrier wait
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
@@ -80,366 +83,421 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsig
   return false;
 }
 
-// Shared-memory layout of one stage (bytes), given the lattice.
+// Shared-memory layout of one stage.  Rows are stored at a compile-time
+// pitch (PITCH elements >= nx) so that every shared-memory address below is
+// a register plus an immediate.
+template <class LAT, class ST, bool ODD, int PITCH>
 struct RowLayout {
-  int nx;
-  int pop_bytes;   // one population row
-  int eps_rows;    // phi_ref rows staged (9 odd / 5 even in 3D; 3 in 2D)
-  int deps_rows;   // d_t phi rows staged (5 in 3D, 3 in 2D; 0 if static)
-  int stage_bytes;
+  static constexpr int kEpsRows = LAT::D == 2 ? 3 : (ODD ? 9 : 5);
+  static constexpr int kDepsRows = LAT::D == 2 ? 3 : 5;
+  static constexpr int kPopBytes = PITCH * (int)sizeof(ST);
+  static constexpr int kRowBytes = PITCH * 4;
+  static constexpr int kEpsOff = LAT::Q * kPopBytes;
+  static constexpr int kDepsOff = kEpsOff + kEpsRows * kRowBytes;
+  static constexpr int kStageBytes = kDepsOff + kDepsRows * kRowBytes;
+  static constexpr int kCopiesMax = LAT::Q + kEpsRows + kDepsRows;
 };
 
-template <class LAT, class ST, bool ODD>
-__host__ __device__ inline RowLayout row_layout(int nx, bool tv) {
-  RowLayout r;
-  r.nx = nx;
-  r.pop_bytes = nx * (int)sizeof(ST);
-  r.eps_rows = LAT::D == 2 ? 3 : (ODD ? 9 : 5);
-  r.deps_rows = tv ? (LAT::D == 2 ? 3 : 5) : 0;
-  r.stage_bytes = LAT::Q * r.pop_bytes + (r.eps_rows + r.deps_rows) * nx * 4;
-  return r;
-}
-
-// Index of the phi_ref row (dy, dz) inside a stage.
+// Index of the phi_ref row (dy, dz) inside a stage: 3x3 block at odd steps
+// (3D), 5-point cross at even steps (3D), 3 rows in 2D.
 template <class LAT, bool ODD>
-__device__ __forceinline__ int eps_row_index(int dy, int dz) {
-  if (LAT::D == 2) return dy + 1;
-  if (ODD) return (dz + 1) * 3 + (dy + 1);
-  // 5-point cross: 0 centre, 1 y-1, 2 y+1, 3 z-1, 4 z+1
-  return dz == 0 ? (dy == 0 ? 0 : (dy < 0 ? 1 : 2)) : (dz < 0 ? 3 : 4);
+__host__ __device__ constexpr int eps_row_index(int dy, int dz) {
+  return LAT::D == 2 ? dy + 1
+                     : (ODD ? (dz + 1) * 3 + (dy + 1)
+                            : (dz == 0 ? (dy == 0 ? 0 : (dy < 0 ? 1 : 2)) : (dz < 0 ? 3 : 4)));
 }
 
-// Index of the d_t phi row (dy, dz) (5-point cross; 2D: dy only).
+// Index of the d_t phi row (dy, dz): 5-point cross (3D), 3 rows (2D).
 template <class LAT>
-__device__ __forceinline__ int deps_row_index(int dy, int dz) {
-  if (LAT::D == 2) return dy + 1;
-  return dz == 0 ? (dy == 0 ? 0 : (dy < 0 ? 1 : 2)) : (dz < 0 ? 3 : 4);
-}
-
-struct RowGeom {
-  int y0, nyf, z0, nzf;  // fluid rows: y in [y0, y0+nyf), z in [z0, z0+nzf)
-};
-
-__device__ __forceinline__ RowGeom row_geom(const LatticeDev &L) {
-  RowGeom g;
-  const bool wy = (L.walls & 2u) != 0, wz = (L.walls & 4u) != 0;
-  g.y0 = wy ? 1 : 0;
-  g.nyf = wy ? L.ny - 2 : L.ny;
-  g.z0 = wz ? 1 : 0;
-  g.nzf = wz ? L.nz - 2 : L.nz;
-  return g;
+__host__ __device__ constexpr int deps_row_index(int dy, int dz) {
+  return LAT::D == 2 ? dy + 1 : (dz == 0 ? (dy == 0 ? 0 : (dy < 0 ? 1 : 2)) : (dz < 0 ? 3 : 4));
 }
 
 __device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
-__device__ __forceinline__ bool row_solid(const LatticeDev &L, int y, int z) {
-  return ((L.walls & 2u) && (y <= 0 || y >= L.ny - 1)) || ((L.walls & 4u) && (z <= 0 || z >= L.nz - 1));
+// Per-row quantities shared by the block (computed once per row).
+struct RowCtx {
+  int base[3][3];   // cell index of x = 0 on row (y+dy, z+dz), [dz+1][dy+1]
+  unsigned solid;   // bit (dz+1)*3+(dy+1): that neighbour row is a wall layer
+};
+
+__device__ __forceinline__ RowCtx make_row_ctx(const LatticeDev &L, int y, int z) {
+  RowCtx c;
+  c.solid = 0;
+  for (int dz = -1; dz <= 1; ++dz)
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int yy = wrapi(y + dy, L.ny), zz = wrapi(z + dz, L.nz);
+      c.base[dz + 1][dy + 1] = (zz * L.ny + yy) * L.nx;
+      const bool sol = ((L.walls & 2u) && (y + dy <= 0 || y + dy >= L.ny - 1)) ||
+                       ((L.walls & 4u) && (z + dz <= 0 || z + dz >= L.nz - 1));
+      if (sol) c.solid |= 1u << ((dz + 1) * 3 + (dy + 1));
+    }
+  return c;
 }
 
-// Thread 0: issue every bulk copy of row (y, z) into `stage`.
-template <class LAT, class ST, bool ODD>
-__device__ __forceinline__ void issue_row(const LatticeDev &L, const RowLayout &lay, unsigned char *stage,
-                                          unsigned long long *bar, int y, int z) {
+// Warp 0: issue every bulk copy of a row into `stage`, one copy per lane.
+template <class LAT, class ST, bool ODD, int PITCH>
+__device__ __forceinline__ void issue_row(const LatticeDev &L, unsigned char *stage, unsigned long long *bar,
+                                          const RowCtx &rc) {
+  using Lay = RowLayout<LAT, ST, ODD, PITCH>;
+  const int lane = threadIdx.x & 31;
   const bool tv = L.has_deps != 0;
-  const int nx = L.nx, ny = L.ny, nz = L.nz;
-  const unsigned total = (unsigned)lay.stage_bytes;
-  mbar_arrive_expect_tx(bar, total);
+  const int nx = L.nx;
+  const unsigned pbytes = (unsigned)nx * (unsigned)sizeof(ST), rbytes = (unsigned)nx * 4u;
+  const int ncopies = LAT::Q + Lay::kEpsRows + (tv ? Lay::kDepsRows : 0);
+  if (lane == 0)
+    mbar_arrive_expect_tx(bar, (unsigned)LAT::Q * pbytes + (unsigned)(ncopies - LAT::Q) * rbytes);
+  __syncwarp();
   const ST *pop = static_cast<const ST *>(L.pop);
-  const long long plane = L.plane;
-  for (int i = 0; i < LAT::Q; ++i) {
-    int plane_i = i, yy = y, zz = z;
-    if (ODD && i != 0) {
-      const int cy = LAT::c(i, 1), cz = LAT::c(i, 2);
-      const int ys = wrapi(y - cy, ny), zs = LAT::D == 3 ? wrapi(z - cz, nz) : z;
-      if (!row_solid(L, ys, zs)) {
-        plane_i = opp_of(i);
-        yy = ys;
-        zz = zs;
-      }
-    }
-    const ST *src = pop + (long long)plane_i * plane + ((long long)zz * ny + yy) * nx;
-    bulk_g2s(stage + i * lay.pop_bytes, src, (unsigned)lay.pop_bytes, bar);
-  }
   const float *eps = static_cast<const float *>(L.eps);
-  unsigned char *erow = stage + LAT::Q * lay.pop_bytes;
-  const unsigned rb = (unsigned)nx * 4u;
-  if (LAT::D == 2) {
-    for (int dy = -1; dy <= 1; ++dy)
-      bulk_g2s(erow + (dy + 1) * rb, eps + (long long)wrapi(y + dy, ny) * nx, rb, bar);
-  } else if (ODD) {
-    for (int dz = -1; dz <= 1; ++dz)
-      for (int dy = -1; dy <= 1; ++dy)
-        bulk_g2s(erow + ((dz + 1) * 3 + (dy + 1)) * rb,
-                 eps + ((long long)wrapi(z + dz, nz) * ny + wrapi(y + dy, ny)) * nx, rb, bar);
-  } else {
-    const int dys[5] = {0, -1, 1, 0, 0}, dzs[5] = {0, 0, 0, -1, 1};
-    for (int j = 0; j < 5; ++j)
-      bulk_g2s(erow + j * rb, eps + ((long long)wrapi(z + dzs[j], nz) * ny + wrapi(y + dys[j], ny)) * nx, rb,
-               bar);
-  }
-  if (tv) {
-    const float *deps = static_cast<const float *>(L.deps);
-    unsigned char *drow = erow + lay.eps_rows * rb;
-    const int nd = LAT::D == 2 ? 3 : 5;
-    const int dys[5] = {0, -1, 1, 0, 0}, dzs[5] = {0, 0, 0, -1, 1};
-    for (int j = 0; j < nd; ++j) {
-      const int dy = LAT::D == 2 ? j - 1 : dys[j], dz = LAT::D == 2 ? 0 : dzs[j];
-      bulk_g2s(drow + j * rb, deps + ((long long)wrapi(z + dz, nz) * ny + wrapi(y + dy, ny)) * nx, rb, bar);
+  const float *deps = static_cast<const float *>(L.deps);
+  for (int j = lane; j < ncopies; j += 32) {
+    if (j < LAT::Q) {
+      const int i = j;
+      int plane_i = i, dy = 0, dz = 0;
+      if (ODD && i != 0) {
+        const int cy = LAT::c(i, 1), cz = LAT::c(i, 2);
+        if (!((rc.solid >> ((1 - cz) * 3 + (1 - cy))) & 1u)) {
+          plane_i = opp_of(i);
+          dy = -cy;
+          dz = -cz;
+        }
+      }
+      const ST *src = pop + (long long)plane_i * L.plane + rc.base[dz + 1][dy + 1];
+      bulk_g2s(stage + i * Lay::kPopBytes, src, pbytes, bar);
+    } else if (j < LAT::Q + Lay::kEpsRows) {
+      const int e = j - LAT::Q;
+      int dy, dz;
+      if (LAT::D == 2) {
+        dy = e - 1;
+        dz = 0;
+      } else if (ODD) {
+        dy = e % 3 - 1;
+        dz = e / 3 - 1;
+      } else {
+        const int dys[5] = {0, -1, 1, 0, 0}, dzs[5] = {0, 0, 0, -1, 1};
+        dy = dys[e];
+        dz = dzs[e];
+      }
+      bulk_g2s(stage + Lay::kEpsOff + e * Lay::kRowBytes, eps + rc.base[dz + 1][dy + 1], rbytes, bar);
+    } else {
+      const int e = j - LAT::Q - Lay::kEpsRows;
+      int dy, dz;
+      if (LAT::D == 2) {
+        dy = e - 1;
+        dz = 0;
+      } else {
+        const int dys[5] = {0, -1, 1, 0, 0}, dzs[5] = {0, 0, 0, -1, 1};
+        dy = dys[e];
+        dz = dzs[e];
+      }
+      bulk_g2s(stage + Lay::kDepsOff + e * Lay::kRowBytes, deps + rc.base[dz + 1][dy + 1], rbytes, bar);
     }
   }
 }
 
-// Update the cells of row (y, z) owned by this thread from a staged row.
-template <class LAT, class ST, bool ODD, bool RED>
-__device__ __forceinline__ void update_row_cells(const LatticeDev &L, const RowLayout &lay,
-                                                 const unsigned char *stage, long long n, int y, int z,
-                                                 RedAcc &acc) {
+// Update the 32-cell chunk [x0, x0 + 32) of one staged row (one cell per
+// lane).
+template <class LAT, class ST, bool ODD, bool RED, bool WALLS, int PITCH>
+__device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsigned char *stage,
+                                                 const RowCtx &rc, long long n, int x, RedAcc &acc) {
+  using Lay = RowLayout<LAT, ST, ODD, PITCH>;
   constexpr int Q = LAT::Q, D = LAT::D;
-  const int nx = L.nx, ny = L.ny, nz = L.nz;
+  constexpr bool kScaled = sizeof(ST) < 4;  // FP16 stores deviations times 2^k
+  const int nx = L.nx;
   const ST *prow = reinterpret_cast<const ST *>(stage);
-  const float *erow = reinterpret_cast<const float *>(stage + Q * lay.pop_bytes);
-  const float *drow = erow + lay.eps_rows * nx;
+  const float *erow = reinterpret_cast<const float *>(stage + Lay::kEpsOff);
+  const float *drow = reinterpret_cast<const float *>(stage + Lay::kDepsOff);
   const bool tv = L.has_deps != 0;
   const float dn = (float)(n - L.n_eps);
   const float rho0 = (float)L.rho0;
   const float inv_scale = L.inv_scale, scale = L.scale;
-  const float *__restrict__ eps_g = static_cast<const float *>(L.eps);
   const float *__restrict__ srd = L.sig_rd;
-  const bool reshift = srd != eps_g;  // shift changed by the last set_epsilon
-  const unsigned walls = L.walls;
+  const bool reshift = srd != static_cast<const float *>(L.eps);
   ST *__restrict__ pop = static_cast<ST *>(L.pop);
-  const long long plane = L.plane;
-  const int ym = wrapi(y - 1, ny), yp = wrapi(y + 1, ny);
-  const int zm = D == 3 ? wrapi(z - 1, nz) : z, zp = D == 3 ? wrapi(z + 1, nz) : z;
-  const int rowbase = (z * ny + y) * nx;
-  // sigma (phi_ref) on the staged rows; reshift steps read sigma_rd from global
-  auto E = [&](int dy, int dz, int xx) -> float { return erow[eps_row_index<LAT, ODD>(dy, dz) * nx + xx]; };
-  auto Dd = [&](int dy, int dz, int xx) -> float { return drow[deps_row_index<LAT>(dy, dz) * nx + xx]; };
+  const int plane = (int)L.plane;
+  const float omega = (float)L.omega;
+  const float om1 = 1.0f - omega;
+  const float cf3 = 3.0f * (float)L.cf, cf9 = 9.0f * (float)L.cf;
+  const unsigned qa = L.quad_axes;
 
-  for (int x = threadIdx.x; x < nx; x += blockDim.x) {
-    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-    const int xs[3] = {xm, x, xp};
-    const int ys_[3] = {ym, y, yp};
-    const int zs_[3] = {zm, z, zp};
-    const int cell = rowbase + x;
-    float s_x = rho0 * (reshift ? __ldg(srd + cell) : E(0, 0, x));
+#define EPS_AT(dy, dz, xx) erow[eps_row_index<LAT, ODD>((dy), (dz)) * PITCH + (xx)]
+#define DEPS_AT(dy, dz, xx) drow[deps_row_index<LAT>((dy), (dz)) * PITCH + (xx)]
+  // slot of population i read from / written to this cell's own memory?
+#define OWN_SRC(i) (!ODD || (i) == 0 || (WALLS && ((rc.solid >> ((1 - LAT::c((i), 2)) * 3 + (1 - LAT::c((i), 1)))) & 1u)))
+#define OWN_DST(i) (!ODD || (i) == 0 || (WALLS && ((rc.solid >> ((1 + LAT::c((i), 2)) * 3 + (1 + LAT::c((i), 1)))) & 1u)))
 
-    // 1. decode
-    float d[Q];
+  const int xs[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};
+  const int cell = rc.base[1][1] + x;
+  const float e_own = EPS_AT(0, 0, x);
+  // the cell's frame: its own shift as stored (sigma_rd)
+  const float s_x = rho0 * (reshift ? __ldg(srd + cell) : e_own);
+
+  // 1. decode: d_i = f_i/w_i - s_x.  A value stored in another cell m carries
+  //    that cell's shift: add delta_i = rho0 sigma(m) - s_x (exact product in
+  //    the FMA; the encode below uses the same form, so the round trip is
+  //    exact up to the final rounding).  Own-cell values need no shift.
+  float d[Q], delta[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const int cx = LAT::c(i, 0), cy = LAT::c(i, 1), cz = LAT::c(i, 2);
-      if (!ODD || i == 0) {
-        d[i] = PopIO<ST>::ld(prow + i * nx + x) * inv_scale;
-      } else if (walls && row_solid(L, ys_[1 - cy], zs_[1 - cz])) {
-        d[i] = PopIO<ST>::ld(prow + i * nx + x) * inv_scale;
-      } else {
-        const int xsrc = xs[1 - cx];
-        float sm;
-        if (reshift)
-          sm = __ldg(srd + (zs_[1 - cz] * ny + ys_[1 - cy]) * nx + xsrc);
-        else
-          sm = E(-cy, -cz, xsrc);
-        d[i] = fmaf(PopIO<ST>::ld(prow + i * nx + xsrc), inv_scale, rho0 * sm - s_x);
-      }
-    }
-
-    // 2. moments
-    float dM = 0.f, j0 = 0.f, j1 = 0.f, j2 = 0.f;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const float wd = (float)LAT::w(i) * d[i];
-      dM += wd;
-      if (LAT::c(i, 0) == 1) j0 += wd;
-      if (LAT::c(i, 0) == -1) j0 -= wd;
-      if (LAT::c(i, 1) == 1) j1 += wd;
-      if (LAT::c(i, 1) == -1) j1 -= wd;
-      if (D == 3 && LAT::c(i, 2) == 1) j2 += wd;
-      if (D == 3 && LAT::c(i, 2) == -1) j2 -= wd;
-    }
-    const float M0 = s_x + dM;
-
-    // 3. phi at time n on the stencil (staged rows)
-    auto phi = [&](int dy, int dz, int xx) {
-      float e = E(dy, dz, xx);
-      if (tv) e = fmaf(dn, Dd(dy, dz, xx), e);
-      return e;
-    };
-    const float e_c = phi(0, 0, x);
-    const float e_xp = phi(0, 0, xp), e_xm = phi(0, 0, xm);
-    const float e_yp = phi(1, 0, x), e_ym = phi(-1, 0, x);
-    float e_zp = e_c, e_zm = e_c;
-    if (D == 3) {
-      e_zp = phi(0, 1, x);
-      e_zm = phi(0, -1, x);
-    }
-
-    // 4.-6. quadrature, density, forces, velocity
-    const unsigned qa = L.quad_axes;
-    float nb = 0.f;
-    if (qa & 1u) nb += e_xp + e_xm;
-    if (qa & 2u) nb += e_yp + e_ym;
-    if (qa & 4u) nb += e_zp + e_zm;
-    const float I = (float)L.qw0 * e_c + (float)L.qw1 * nb;
-    const float rho = M0 / I;
-    const float pc = rho * (1.0f / 3.0f);
-    float F0 = (float)L.g[0] + pc * 0.5f * (e_xp - e_xm);
-    float F1 = (float)L.g[1] + pc * 0.5f * (e_yp - e_ym);
-    float F2 = D == 3 ? (float)L.g[2] + pc * 0.5f * (e_zp - e_zm) : 0.f;
-    if (L.has_force) {
-      const float *__restrict__ fo = static_cast<const float *>(L.force);
-      const long long N = L.ncell;
-      float a0 = __ldg(fo + cell), a1 = __ldg(fo + N + cell), a2 = D == 3 ? __ldg(fo + 2 * N + cell) : 0.f;
-      if (L.has_dforce) {
-        const float *__restrict__ df = static_cast<const float *>(L.dforce);
-        const float dnf = (float)(n - L.n_force);
-        a0 = fmaf(dnf, __ldg(df + cell), a0);
-        a1 = fmaf(dnf, __ldg(df + N + cell), a1);
-        if (D == 3) a2 = fmaf(dnf, __ldg(df + 2 * N + cell), a2);
-      }
-      F0 += a0;
-      F1 += a1;
-      F2 += a2;
-    }
-    const float invM = 1.0f / M0;
-    const float u0 = (j0 + 0.5f * F0) * invM;
-    const float u1 = (j1 + 0.5f * F1) * invM;
-    const float u2 = D == 3 ? (j2 + 0.5f * F2) * invM : 0.f;
-    const float usq = u0 * u0 + u1 * u1 + u2 * u2;
-    const float uF = u0 * F0 + u1 * F1 + u2 * F2;
-
-    if (RED) {
-      const double m0 = (double)M0;
-      acc.v[0] += m0;
-      acc.v[1] += m0 * (double)u0;
-      acc.v[2] += m0 * (double)u1;
-      acc.v[3] += m0 * (double)u2;
-      acc.v[5] += (double)usq;
-      if (L.u_prev) {
-        float *up = L.u_prev;
-        const long long N = L.ncell;
-        if (L.have_prev) {
-          const double a = (double)u0 - (double)up[cell];
-          const double b = (double)u1 - (double)up[N + cell];
-          const double c = (double)u2 - (double)up[2 * N + cell];
-          acc.v[4] += a * a + b * b + c * c;
-        }
-        up[cell] = u0;
-        up[N + cell] = u1;
-        up[2 * N + cell] = u2;
-      }
-      if (!isfinite(M0) || !isfinite(usq)) acc.v[6] += 1.0;
-      acc.v[7] += (double)F0;
-      acc.v[8] += (double)F1;
-      acc.v[9] += (double)F2;
-    }
-
-    // 7.-8. collide and stream; the new shift is phi_ref (staged)
-    const float omega = (float)L.omega, cf = (float)L.cf;
-    const float s_new_x = rho0 * E(0, 0, x);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const int cx = LAT::c(i, 0), cy = LAT::c(i, 1), cz = LAT::c(i, 2);
-      float cu = 0.f, cF = 0.f;
-      if (cx == 1) { cu += u0; cF += F0; }
-      if (cx == -1) { cu -= u0; cF -= F0; }
-      if (cy == 1) { cu += u1; cF += F1; }
-      if (cy == -1) { cu -= u1; cF -= F1; }
-      if (cz == 1) { cu += u2; cF += F2; }
-      if (cz == -1) { cu -= u2; cF -= F2; }
-      const float pm1 = cu * fmaf(4.5f, cu, 3.0f) - 1.5f * usq;
-      const float deq = fmaf(M0, pm1, dM);
-      const float src = cf * fmaf(9.0f * cu, cF, 3.0f * (cF - uF));
-      // d*_i = f*_i/w_i - s_x, re-encoded against the storage cell's new
-      // shift by adding the (small) shift difference, never by subtracting
-      // two O(1) numbers
-      const float dstar = fmaf(omega, deq - d[i], d[i]) + src;
-      if (!ODD || i == 0) {
-        PopIO<ST>::st(pop + (long long)opp_of(i) * plane + cell, (dstar + (s_x - s_new_x)) * scale);
-      } else if (walls && row_solid(L, ys_[1 + cy], zs_[1 + cz])) {
-        PopIO<ST>::st(pop + (long long)opp_of(i) * plane + cell, (dstar + (s_x - s_new_x)) * scale);
-      } else {
-        const int m = (zs_[1 + cz] * ny + ys_[1 + cy]) * nx + xs[1 + cx];
-        const float s_m = rho0 * E(cy, cz, xs[1 + cx]);
-        PopIO<ST>::st(pop + (long long)i * plane + m, (dstar + (s_x - s_m)) * scale);
-      }
+  for (int i = 0; i < Q; ++i) {
+    const int cx = LAT::c(i, 0), cy = LAT::c(i, 1), cz = LAT::c(i, 2);
+    const bool own = OWN_SRC(i);
+    const float q = PopIO<ST>::ld(prow + i * PITCH + (own ? x : xs[1 - cx]));
+    const float qs = kScaled ? q * inv_scale : q;
+    if (own) {
+      delta[i] = 0.f;
+      d[i] = qs;
+    } else {
+      const float sm = reshift ? __ldg(srd + rc.base[1 - cz][1 - cy] + xs[1 - cx]) : EPS_AT(-cy, -cz, xs[1 - cx]);
+      delta[i] = fmaf(rho0, sm, -s_x);
+      d[i] = qs + delta[i];
     }
   }
+
+  // 2. moments: dM = sum w d, J = sum w xi d
+  float dM = 0.f, j0 = 0.f, j1 = 0.f, j2 = 0.f;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const float w = (float)LAT::w(i);
+    dM = fmaf(w, d[i], dM);
+    if (LAT::c(i, 0) != 0) j0 = fmaf(LAT::c(i, 0) > 0 ? w : -w, d[i], j0);
+    if (LAT::c(i, 1) != 0) j1 = fmaf(LAT::c(i, 1) > 0 ? w : -w, d[i], j1);
+    if (D == 3 && LAT::c(i, 2) != 0) j2 = fmaf(LAT::c(i, 2) > 0 ? w : -w, d[i], j2);
+  }
+  const float M0 = s_x + dM;
+
+  // 3. phi at time n on the stencil
+  float e_c = e_own, e_xp = EPS_AT(0, 0, xs[2]), e_xm = EPS_AT(0, 0, xs[0]);
+  float e_yp = EPS_AT(1, 0, x), e_ym = EPS_AT(-1, 0, x);
+  float e_zp = e_c, e_zm = e_c;
+  if (D == 3) {
+    e_zp = EPS_AT(0, 1, x);
+    e_zm = EPS_AT(0, -1, x);
+  }
+  if (tv) {
+    e_c = fmaf(dn, DEPS_AT(0, 0, x), e_c);
+    e_xp = fmaf(dn, DEPS_AT(0, 0, xs[2]), e_xp);
+    e_xm = fmaf(dn, DEPS_AT(0, 0, xs[0]), e_xm);
+    e_yp = fmaf(dn, DEPS_AT(1, 0, x), e_yp);
+    e_ym = fmaf(dn, DEPS_AT(-1, 0, x), e_ym);
+    if (D == 3) {
+      e_zp = fmaf(dn, DEPS_AT(0, 1, x), e_zp);
+      e_zm = fmaf(dn, DEPS_AT(0, -1, x), e_zm);
+    }
+  }
+
+  // 4.-6. quadrature, density, forces, velocity
+  float nb = 0.f;
+  if (qa & 1u) nb += e_xp + e_xm;
+  if (qa & 2u) nb += e_yp + e_ym;
+  if (qa & 4u) nb += e_zp + e_zm;
+  const float I = fmaf((float)L.qw0, e_c, (float)L.qw1 * nb);
+  const float pc2 = M0 / I * (0.5f / 3.0f);  // c_s^2 rho~ / 2
+  float F0 = fmaf(pc2, e_xp - e_xm, (float)L.g[0]);
+  float F1 = fmaf(pc2, e_yp - e_ym, (float)L.g[1]);
+  float F2 = D == 3 ? fmaf(pc2, e_zp - e_zm, (float)L.g[2]) : 0.f;
+  if (L.has_force) {
+    const float *__restrict__ fo = static_cast<const float *>(L.force);
+    const int N = (int)L.ncell;
+    float a0 = __ldg(fo + cell), a1 = __ldg(fo + N + cell), a2 = D == 3 ? __ldg(fo + 2 * N + cell) : 0.f;
+    if (L.has_dforce) {
+      const float *__restrict__ df = static_cast<const float *>(L.dforce);
+      const float dnf = (float)(n - L.n_force);
+      a0 = fmaf(dnf, __ldg(df + cell), a0);
+      a1 = fmaf(dnf, __ldg(df + N + cell), a1);
+      if (D == 3) a2 = fmaf(dnf, __ldg(df + 2 * N + cell), a2);
+    }
+    F0 += a0;
+    F1 += a1;
+    F2 += a2;
+  }
+  const float invM = 1.0f / M0;
+  const float u0 = fmaf(0.5f, F0, j0) * invM;
+  const float u1 = fmaf(0.5f, F1, j1) * invM;
+  const float u2 = D == 3 ? fmaf(0.5f, F2, j2) * invM : 0.f;
+  const float usq = fmaf(u0, u0, fmaf(u1, u1, u2 * u2));
+  const float uF = fmaf(u0, F0, fmaf(u1, F1, u2 * F2));
+
+  if (RED) {
+    const double m0 = (double)M0;
+    acc.v[0] += m0;
+    acc.v[1] += m0 * (double)u0;
+    acc.v[2] += m0 * (double)u1;
+    acc.v[3] += m0 * (double)u2;
+    acc.v[5] += (double)usq;
+    if (L.u_prev) {
+      float *up = L.u_prev;
+      const int N = (int)L.ncell;
+      if (L.have_prev) {
+        const double a = (double)u0 - (double)up[cell];
+        const double b = (double)u1 - (double)up[N + cell];
+        const double c = (double)u2 - (double)up[2 * N + cell];
+        acc.v[4] += a * a + b * b + c * c;
+      }
+      up[cell] = u0;
+      up[N + cell] = u1;
+      up[2 * N + cell] = u2;
+    }
+    if (!isfinite(M0) || !isfinite(usq)) acc.v[6] += 1.0;
+    acc.v[7] += (double)F0;
+    acc.v[8] += (double)F1;
+    acc.v[9] += (double)F2;
+  }
+
+  // 7.-8. collide and stream:
+  //   d*_i = (1 - omega) d_i + omega (dM + M0 (3 cu + 4.5 cu^2 - 1.5 u.u))
+  //          + (1 - 1/(2 tau)) (3 (cF - u.F) + 9 cu cF)
+  //   stored: d*_i + s_x - rho0 sigma_wr(storage cell).  sigma_wr is the new
+  //   phi_ref; without a pending shift change it equals sigma_rd, and the
+  //   shift difference of the neighbour x + xi_i is -delta of the opposite
+  //   direction.
+  const float m15usq = -1.5f * usq;
+  const float m3uF = -cf3 * uF;
+  const float enc_own = reshift ? fmaf(-rho0, e_own, s_x) : 0.f;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int cx = LAT::c(i, 0), cy = LAT::c(i, 1), cz = LAT::c(i, 2);
+    float cu = 0.f, cF = 0.f;
+    if (cx == 1) { cu += u0; cF += F0; }
+    if (cx == -1) { cu -= u0; cF -= F0; }
+    if (cy == 1) { cu += u1; cF += F1; }
+    if (cy == -1) { cu -= u1; cF -= F1; }
+    if (cz == 1) { cu += u2; cF += F2; }
+    if (cz == -1) { cu -= u2; cF -= F2; }
+    const float pm1 = fmaf(cu, fmaf(4.5f, cu, 3.0f), m15usq);
+    const float deq = fmaf(M0, pm1, dM);
+    const float src = fmaf(cu * cf9, cF, fmaf(cf3, cF, m3uF));
+    const float dstar = fmaf(om1, d[i], fmaf(omega, deq, src));
+    if (OWN_DST(i)) {
+      const float v = dstar + enc_own;
+      PopIO<ST>::st(pop + opp_of(i) * plane + cell, kScaled ? v * scale : v);
+    } else {
+      const int xm = xs[1 + cx];
+      float enc;
+      if (!reshift && !OWN_SRC(opp_of(i)))
+        enc = -delta[opp_of(i)];
+      else
+        enc = fmaf(-rho0, EPS_AT(cy, cz, xm), s_x);
+      const float v = dstar + enc;
+      PopIO<ST>::st(pop + i * plane + rc.base[1 + cz][1 + cy] + xm, kScaled ? v * scale : v);
+    }
+  }
+#undef EPS_AT
+#undef DEPS_AT
+#undef OWN_SRC
+#undef OWN_DST
 }
 
-template <class LAT, class ST, bool ODD, bool RED, int MINB>
-__global__ void __launch_bounds__(kRowThreads, MINB) step_row_kernel(const LatticeDev *__restrict__ Lp, int k) {
-  constexpr int NSTAGE = 2;
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait that also gives up when another warp has raised `abort`.
+__device__ __forceinline__ bool mbar_wait_or_abort(unsigned long long *bar, unsigned parity, unsigned limit,
+                                                   volatile int *abort) {
+  for (unsigned i = 0; i < limit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort) return false;
+  }
+  return false;
+}
+
+// Warp-specialised row kernel.  Warp kConsumerWarps is the producer: it
+// stages row j into stage j % NSTAGE once the consumers have released the
+// row that used it before (empty barrier), arming the full barrier with the
+// byte count of the copies.  The consumer warps wait on the full barrier,
+// update their cells and release the stage, one arrival per warp.  No
+// block-wide barrier is taken inside the loop.
+template <class LAT, class ST, bool ODD, bool RED, bool WALLS, int PITCH, int NSTAGE, int MINB>
+__global__ void __launch_bounds__(kRowBlock, MINB) step_row_kernel(const LatticeDev *__restrict__ Lp, int k) {
+  using Lay = RowLayout<LAT, ST, ODD, PITCH>;
   __shared__ LatticeDev Ls;
-  __shared__ alignas(8) unsigned long long bars[NSTAGE];
-  __shared__ int s_abort;
+  __shared__ alignas(8) unsigned long long full[NSTAGE];
+  __shared__ alignas(8) unsigned long long empty[NSTAGE];
+  __shared__ RowCtx ctx[NSTAGE];
+  __shared__ volatile int abort_flag;
   extern __shared__ __align__(128) unsigned char stages[];
   const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
   {
     const int *src = reinterpret_cast<const int *>(Lp);
     int *dst = reinterpret_cast<int *>(&Ls);
     for (int w = tid; w < (int)(sizeof(LatticeDev) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
   }
   if (tid == 0) {
-    for (int s = 0; s < NSTAGE; ++s) mbar_init(&bars[s], 1);
+    for (int s = 0; s < NSTAGE; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kConsumerWarps);
+    }
+    abort_flag = 0;
     mbar_fence_init();
-    s_abort = 0;
   }
   __syncthreads();
   const LatticeDev &L = Ls;
-  const RowLayout lay = row_layout<LAT, ST, ODD>(L.nx, L.has_deps != 0);
-  const RowGeom gm = row_geom(L);
-  const int nrows = gm.nyf * gm.nzf;
-  const long long n = L.n + k;
+  const bool wy = (L.walls & 2u) != 0, wz = (L.walls & 4u) != 0;
+  const int y0 = wy ? 1 : 0, nyf = wy ? L.ny - 2 : L.ny;
+  const int z0 = wz ? 1 : 0, nzf = wz ? L.nz - 2 : L.nz;
+  const int nrows = nyf * nzf;
+  const unsigned limit = L.wait_limit;
   RedAcc acc;
 #pragma unroll
   for (int j = 0; j < kRedWidth; ++j) acc.v[j] = 0.0;
 
-  auto row_yz = [&](int r, int &y, int &z) {
-    y = gm.y0 + r % gm.nyf;
-    z = gm.z0 + r / gm.nyf;
-  };
-  // prologue: rows of the first NSTAGE-1 iterations
-  if (tid == 0) {
-    for (int j = 0; j < NSTAGE - 1; ++j) {
-      const int r = blockIdx.x + j * gridDim.x;
-      if (r < nrows) {
-        int y, z;
-        row_yz(r, y, z);
-        issue_row<LAT, ST, ODD>(L, lay, stages + j * lay.stage_bytes, &bars[j], y, z);
-      }
-    }
-  }
-  int it = 0;
-  for (int r = blockIdx.x; r < nrows; r += gridDim.x, ++it) {
-    const int s = it % NSTAGE;
-    if (tid == 0) {
-      const int rn = r + (NSTAGE - 1) * gridDim.x;
-      const int sn = (it + NSTAGE - 1) % NSTAGE;
-      if (rn < nrows) {
-        int y, z;
-        row_yz(rn, y, z);
-        issue_row<LAT, ST, ODD>(L, lay, stages + sn * lay.stage_bytes, &bars[sn], y, z);
-      }
-    }
-    const bool ok = mbar_wait_bounded(&bars[s], (unsigned)((it / NSTAGE) & 1), L.wait_limit);
-    if (__syncthreads_or(!ok)) {
-      // a copy never completed: record it, drain what is in flight, leave
-      if (tid == 0) {
-        atomicExch(L.status, 1);
-        for (int j = 0; j < NSTAGE; ++j) {
-          const int rj = r + j * gridDim.x;
-          if (rj < nrows) mbar_wait_bounded(&bars[(it + j) % NSTAGE], (unsigned)(((it + j) / NSTAGE) & 1));
+  if (warp == kConsumerWarps) {
+    // ---------------- producer warp
+    const bool withhold = L.withhold_copies != 0;
+    int issued_upto = -1;  // last row index j whose copies were issued
+    int j = 0;
+    for (int r = blockIdx.x; r < nrows; r += gridDim.x, ++j) {
+      const int s = j % NSTAGE;
+      if (j >= NSTAGE) {
+        // the consumers released row j - NSTAGE from this stage
+        if (!mbar_wait_or_abort(&empty[s], (unsigned)(((j / NSTAGE) - 1) & 1), limit, &abort_flag)) {
+          if (lane == 0 && !abort_flag) {
+            abort_flag = 1;
+            atomicExch(L.status, 1);
+          }
+          break;
         }
       }
-      __syncthreads();
-      return;
+      if (lane == 0) ctx[s] = make_row_ctx(L, y0 + r % nyf, z0 + r / nyf);
+      __syncwarp();
+      if (!withhold) {
+        issue_row<LAT, ST, ODD, PITCH>(L, stages + s * Lay::kStageBytes, &full[s], ctx[s]);
+        issued_upto = j;
+      }
+      __syncwarp();
     }
-    int y, z;
-    row_yz(r, y, z);
-    update_row_cells<LAT, ST, ODD, RED>(L, lay, stages + s * lay.stage_bytes, n, y, z, acc);
-    __syncthreads();  // every thread is done with stage s before it is refilled
+    if (abort_flag && lane == 0) {
+      // drain: wait (full limit) for every stage whose copies may be in flight
+      for (int jj = issued_upto - NSTAGE + 1; jj <= issued_upto; ++jj)
+        if (jj >= 0) mbar_wait_bounded(&full[jj % NSTAGE], (unsigned)((jj / NSTAGE) & 1));
+    }
+  } else {
+    // ---------------- consumer warps
+    const long long n = L.n + k;
+    int j = 0;
+    for (int r = blockIdx.x; r < nrows; r += gridDim.x, ++j) {
+      const int s = j % NSTAGE;
+      if (!mbar_wait_or_abort(&full[s], (unsigned)((j / NSTAGE) & 1), limit, &abort_flag)) {
+        if (lane == 0 && !abort_flag) {
+          abort_flag = 1;
+          atomicExch(L.status, 1);
+        }
+        break;
+      }
+      // 32-cell chunks of the row, dealt round-robin to the consumer warps
+      // across rows so that every warp gets the same share
+      const int nchunks = L.nx >> 5;
+      const int first = (warp - (int)(((long long)j * nchunks) % kConsumerWarps) + kConsumerWarps) % kConsumerWarps;
+      for (int c = first; c < nchunks; c += kConsumerWarps)
+        update_row_chunk<LAT, ST, ODD, RED, WALLS, PITCH>(L, stages + s * Lay::kStageBytes, ctx[s], n,
+                                                          (c << 5) + lane, acc);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
+    }
   }
+  __syncthreads();
   if (RED) block_reduce_store(acc, L.partials, blockIdx.x);
 }
 
@@ -448,56 +506,88 @@ __global__ void __launch_bounds__(kRowThreads, MINB) step_row_kernel(const Latti
 namespace lbm {
 
 // Host side: launch and planning of the row kernel for one lattice type.
-template <class LAT, class ST, int MINB>
-cudaError_t launch_row_t(const LatticeDev *L_dev, bool odd, int red, int k, const StepLaunch &ls,
+// ls.row encodes the variant: bit 0 set = in use, bit 1 = walls, bit 2 =
+// pitch 512 (else 256).
+template <int P>
+constexpr int row_stages() { return P <= 256 ? 3 : 2; }
+
+template <class LAT, class ST, bool W, int P, int MINB>
+cudaError_t launch_row_v(const LatticeDev *L_dev, bool odd, int red, int k, const StepLaunch &ls,
                          cudaStream_t s) {
-  const int smem = odd ? ls.row_smem_odd : ls.row_smem_even;
-  const dim3 grid(ls.row_grid), block(kRowThreads);
+  constexpr int NS = row_stages<P>();
+  const dim3 grid(ls.row_grid), block(kRowBlock);
   if (odd) {
-    if (red) step_row_kernel<LAT, ST, true, true, MINB><<<grid, block, smem, s>>>(L_dev, k);
-    else step_row_kernel<LAT, ST, true, false, MINB><<<grid, block, smem, s>>>(L_dev, k);
+    const int smem = RowLayout<LAT, ST, true, P>::kStageBytes * NS;
+    if (red) step_row_kernel<LAT, ST, true, true, W, P, NS, MINB><<<grid, block, smem, s>>>(L_dev, k);
+    else step_row_kernel<LAT, ST, true, false, W, P, NS, MINB><<<grid, block, smem, s>>>(L_dev, k);
   } else {
-    if (red) step_row_kernel<LAT, ST, false, true, MINB><<<grid, block, smem, s>>>(L_dev, k);
-    else step_row_kernel<LAT, ST, false, false, MINB><<<grid, block, smem, s>>>(L_dev, k);
+    const int smem = RowLayout<LAT, ST, false, P>::kStageBytes * NS;
+    if (red) step_row_kernel<LAT, ST, false, true, W, P, NS, MINB><<<grid, block, smem, s>>>(L_dev, k);
+    else step_row_kernel<LAT, ST, false, false, W, P, NS, MINB><<<grid, block, smem, s>>>(L_dev, k);
   }
   return cudaGetLastError();
 }
 
 template <class LAT, class ST, int MINB>
+cudaError_t launch_row_t(const LatticeDev *L_dev, bool odd, int red, int k, const StepLaunch &ls,
+                         cudaStream_t s) {
+  const bool w = (ls.row & 2) != 0, p512 = (ls.row & 4) != 0;
+  if (p512) {
+    if (w) return launch_row_v<LAT, ST, true, 512, (MINB > 1 ? MINB - 1 : 1)>(L_dev, odd, red, k, ls, s);
+    return launch_row_v<LAT, ST, false, 512, (MINB > 1 ? MINB - 1 : 1)>(L_dev, odd, red, k, ls, s);
+  }
+  if (w) return launch_row_v<LAT, ST, true, 256, MINB>(L_dev, odd, red, k, ls, s);
+  return launch_row_v<LAT, ST, false, 256, MINB>(L_dev, odd, red, k, ls, s);
+}
+
+template <class LAT, class ST, bool W, int P, int MINB>
+int configure_row_v(int &occ) {
+  constexpr int NS = row_stages<P>();
+  const int smem = RowLayout<LAT, ST, true, P>::kStageBytes * NS;
+  if (smem > 220 * 1024) return 0;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(step_row_kernel<LAT, ST, true, false, W, P, NS, MINB>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(step_row_kernel<LAT, ST, true, true, W, P, NS, MINB>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(step_row_kernel<LAT, ST, false, false, W, P, NS, MINB>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(step_row_kernel<LAT, ST, false, true, W, P, NS, MINB>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step_row_kernel<LAT, ST, true, false, W, P, NS, MINB>,
+                                                      kRowBlock, smem);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return occ >= 1;
+}
+
+template <class LAT, class ST, int MINB>
 int plan_row_t(int nx, int ny, int nz, unsigned walls, StepLaunch &ls) {
-  constexpr int kMaxSmem = 200 * 1024;
-  if (nx % 4 != 0 || (nx * (int)sizeof(ST)) % 16 != 0 || nx > 512 || nx < 32) return 0;
+  if (nx % 32 != 0 || nx > 512 || nx < 32) return 0;
   if (walls & 1u) return 0;
-  const int smem_odd = 2 * row_layout<LAT, ST, true>(nx, true).stage_bytes;
-  const int smem_even = 2 * row_layout<LAT, ST, false>(nx, true).stage_bytes;
-  if (smem_odd > kMaxSmem) return 0;
-  if (cudaFuncSetAttribute(step_row_kernel<LAT, ST, true, false, MINB>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem_odd) != cudaSuccess ||
-      cudaFuncSetAttribute(step_row_kernel<LAT, ST, true, true, MINB>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem_odd) != cudaSuccess ||
-      cudaFuncSetAttribute(step_row_kernel<LAT, ST, false, false, MINB>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem_odd) != cudaSuccess ||
-      cudaFuncSetAttribute(step_row_kernel<LAT, ST, false, true, MINB>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem_odd) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step_row_kernel<LAT, ST, true, false, MINB>,
-                                                    kRowThreads, smem_odd) != cudaSuccess ||
-      occ < 1) {
-    cudaGetLastError();
-    return 0;
-  }
+  const bool w = (walls & 6u) != 0, p512 = nx > 256;
+  int occ = 0, ok;
+  if (p512)
+    ok = w ? configure_row_v<LAT, ST, true, 512, (MINB > 1 ? MINB - 1 : 1)>(occ)
+           : configure_row_v<LAT, ST, false, 512, (MINB > 1 ? MINB - 1 : 1)>(occ);
+  else
+    ok = w ? configure_row_v<LAT, ST, true, 256, MINB>(occ) : configure_row_v<LAT, ST, false, 256, MINB>(occ);
+  if (!ok) return 0;
   const int nyf = (walls & 2u) ? ny - 2 : ny;
   const int nzf = (walls & 4u) ? nz - 2 : nz;
   const int nrows = nyf * nzf;
   if (nrows < 1) return 0;
   const int cap = sm_count() * occ;
-  ls.row = 1;
+  ls.row = 1 | (w ? 2 : 0) | (p512 ? 4 : 0);
   ls.row_grid = nrows < cap ? nrows : cap;
-  ls.row_smem_odd = smem_odd;
-  ls.row_smem_even = smem_even;
+  ls.row_smem_odd = ls.row_smem_even = 0;
   return 1;
 }
 

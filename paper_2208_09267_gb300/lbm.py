@@ -83,7 +83,7 @@ _SIGS = {
     "lbm_vanse_get_populations": (ctypes.c_int, [_H, _P]),
     "lbm_vanse_steps_done": (ctypes.c_longlong, [_H]),
     "lbm_vanse_launch_count": (ctypes.c_longlong, []),
-    "lbm_vanse_set_wait_limit": (ctypes.c_int, [_H, ctypes.c_uint]),
+    "lbm_vanse_set_wait_limit": (ctypes.c_int, [_H, ctypes.c_uint, ctypes.c_int]),
     "lbm_vanse_uses_row_kernel": (ctypes.c_int, [_H]),
     "lbm_vanse_get_params": (ctypes.c_int, [_H, ctypes.POINTER(Params)]),
     "lbm_vanse_save_state": (ctypes.c_int, [_H, _P, ctypes.POINTER(ctypes.c_size_t)]),
@@ -266,8 +266,9 @@ class Lattice:
     def row_kernel(self) -> bool:
         return lib().lbm_vanse_uses_row_kernel(self.handle) == 1
 
-    def set_wait_limit(self, spins: int):
-        _check(lib().lbm_vanse_set_wait_limit(self.handle, int(spins)), self.handle)
+    def set_wait_limit(self, spins: int, withhold_copies: bool = False):
+        _check(lib().lbm_vanse_set_wait_limit(self.handle, int(spins), int(bool(withhold_copies))),
+               self.handle)
 
     @property
     def steps_done(self):
