@@ -255,6 +255,94 @@ def run_gpu(args, rank, world):
     return results, e2e
 
 
+def run_batched(count=64, steps=200, storages=("fp16", "fp32")):
+    """Many independent lattices (half D2Q9 squares of side 32..512, half
+    D3Q19 cubes of side 32..128, product-sine phi, tau in [0.55, 1.2]) advanced
+    together by the batched graph-captured kernels, against the plain
+    per-lattice FP32 path (one handle per lattice, stepped one after the
+    other).  Returns GLUPS and lattices solved per second for each."""
+    import torch
+
+    from paper_2208_09267_gb300 import inputs, lbm
+    specs = inputs.batch_specs(count=count, steps=steps)
+    cells = sum(s.cells for s in specs)
+    stream = torch.cuda.current_stream().cuda_stream
+    out = {"lattices": count, "steps": steps, "cells": cells}
+
+    def make(storage, s):
+        nz, ny, nx = s.shape
+        lat = lbm.Lattice(s.lattice, (nx, ny, nz), tau=s.tau, storage=storage, stream=stream)
+        lat.set_epsilon(eps_of[id(s)])
+        lat.set_force(s.g)
+        lat.init_equilibrium()
+        return lat
+    eps_of = {id(s): s.eps().ravel().astype(np.float32) for s in specs}
+    for storage in storages:
+        lats = [make(storage, s) for s in specs]
+        b = lbm.Batch(max_members=count, max_tiles=sum((lt.n + 4095) // 4096 for lt in lats) + 8,
+                      stream=stream)
+        for lt in lats:
+            b.add(lt, steps + 20)
+        b.step(10)
+        torch.cuda.synchronize()
+        k = 50 if steps % 50 == 0 else 10
+        t = time.perf_counter()
+        for _ in range(steps // k):
+            b.step(k)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        b.close()
+        for lt in lats:
+            lt.close()
+        out[f"batched_{storage}"] = {"glups": cells * steps / dt / 1e9, "solves_per_s": count / dt,
+                                     "seconds": dt}
+    # plain per-lattice FP32: one solver per lattice, each stepped alone
+    lats = [make("fp32", s) for s in specs]
+    for lt in lats:
+        lt.step(10)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for lt in lats:
+        lt.step(steps)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t
+    for lt in lats:
+        lt.close()
+    out["per_lattice_fp32"] = {"glups": cells * steps / dt / 1e9, "solves_per_s": count / dt,
+                               "seconds": dt}
+    return out
+
+
+def run_serving(rate=100.0, count=48, sides=(32, 96), steps=(500, 4000)):
+    """Poisson arrivals of D3Q19 solves (side log-uniform, random-sphere or
+    sine phi, step budget log-uniform or residual 1e-8 with that cap) served
+    with continuous batching in FP16-shifted storage, against plain
+    per-request FP32 (sequential).  Reports solves/s and p50/p99 latency."""
+    import torch
+
+    from paper_2208_09267_gb300 import serve
+    stream = torch.cuda.current_stream().cuda_stream
+    reqs = serve.make_requests(rate, count, sides=sides, steps=steps)
+    srv = serve.Server(storage="fp16", hbm_budget=80e9, macro_steps=100, stream=stream,
+                       keep_results=True)
+    served = srv.run(reqs)
+    srv.close()
+    seq_reqs = [serve.Request(r.rid, r.spec, r.arrival, r.eps) for r in reqs]
+    seq = serve.run_sequential(seq_reqs, storage="fp32", check_every=100, stream=stream)
+    errs = []
+    for a, b in zip(reqs, seq_reqs):
+        if a.result is not None and b.result is not None and a.steps_done == b.steps_done:
+            ua, ub = a.result["u"].astype(np.float64), b.result["u"].astype(np.float64)
+            nb = np.linalg.norm(ub)
+            if nb > 0:
+                errs.append(float(np.linalg.norm(ua - ub) / nb))
+    return {"trace": f"Poisson {rate:g}/s, {count} requests, side log-uniform {sides}, steps "
+                     f"log-uniform {steps} (half with residual 1e-8), 80 GB budget",
+            "served_fp16": served, "sequential_fp32": seq,
+            "fp16_vs_fp32_u_rel_l2_max": max(errs) if errs else None,
+            "fp16_vs_fp32_compared": len(errs)}
+
+
 def cpu_baseline(sample_L=48, steps=None, budget_s=20.0):
     """The FP64 oracle on the host cores, timed on a bounded sample of the
     same workload (a sample_L^3 lattice with the same phi recipe)."""
@@ -291,6 +379,12 @@ def main():
     ap.add_argument("--storages", nargs="+", default=["fp32", "fp16"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--batch-steps", type=int, default=200)
+    ap.add_argument("--serve-count", type=int, default=48)
+    ap.add_argument("--serve-rate", type=float, default=100.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -351,6 +445,10 @@ def main():
                     "kernel_ms": rr["kernel_ms"], "algorithmic_bytes_per_cell": bb,
                     "achieved_gbs": ach, "frac": ach / peak, "gpu_launches": rr["launches"],
                     "traffic": profiled_traffic(st, src_hash), "clocks": rr["clocks"]}
+    if rank == 0 and not args.no_batch:
+        line["batched"] = run_batched(args.batch_count, args.batch_steps)
+    if rank == 0 and not args.no_serve:
+        line["serving"] = run_serving(args.serve_rate, args.serve_count)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(sample_L=48 if L >= 48 else L, budget_s=15.0)
     if rank == 0:

@@ -60,7 +60,11 @@ enum lbm_lattice { LBM_D2Q9 = 0, LBM_D3Q19 = 1, LBM_D3Q27 = 2 };
    canonical evaluation order, bit-identical to the FP64 reference.
    LBM_FP32: the deviation f_i/w_i - rho0*sigma stored in float, collided in
    float.  LBM_FP16_SHIFTED: the same deviation times 2^k stored in IEEE
-   half, collided in float.  sigma is the cell's phi_ref (see set_epsilon). */
+   half, collided in float.  sigma is a per-cell shift, the quadrature
+   int phi_ref dV of eq. (quad) rounded to half: f_i/w_i of the rest state,
+   so that the stored deviations carry the flow signal and not the
+   varpi grad^2 phi part of the zeroth moment.  A value is stored against
+   the shift of the cell whose memory holds it. */
 enum lbm_storage { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16_SHIFTED = 2 };
 
 enum lbm_status {
@@ -102,6 +106,10 @@ typedef struct {
                                shared memory by TMA bulk copies; needs nx a
                                multiple of 4 (FP32) or 8 (FP16), 32 <= nx <= 512,
                                no walls on x; LBM_EINVAL otherwise) */
+  int fp16_rounding;        /* LBM_FP16_SHIFTED stores: 0 = stochastic
+                               rounding (unbiased; random bits from a
+                               counter-based hash of cell and step, so runs
+                               are reproducible), 1 = round to nearest */
 } lbm_vanse_params;
 
 /* Global sums of the state at time n (pre-collision), taken on a check step
@@ -153,8 +161,9 @@ LBM_API void lbm_vanse_destroy(lbm_vanse_t h);
    (Sec. 2.2: phi varies in space and time; the pair is refreshed by the
    caller, and is exact at t = n_ref).  eps_ref: N values in (0, 1];
    deps_dt: N values or NULL for a static field.  The shift sigma of the
-   reduced-precision storages becomes eps_ref: the next step decodes with
-   the previous sigma and encodes with the new one, so no extra pass runs.
+   reduced-precision storages is recomputed from eps_ref: the next step
+   decodes with the previous sigma and encodes with the new one, so no extra
+   pass over the populations runs.
    Errors: LBM_EINVAL if a host-side eps_ref value is not in (0, 1] or not
    finite (device-side inputs are not validated).  The FP64 twin takes
    doubles; on FP32/FP16 handles it rounds them to float. */

@@ -109,6 +109,37 @@ cudaError_t launch_finalize(const double *partials, int nblocks, double *out, cu
   return cudaGetLastError();
 }
 
+__global__ void shift_kernel(const float *eps, __half *sig, int nx, int ny, int nz, unsigned qa, float w0,
+                             float w1) {
+  const long long N = (long long)nx * ny * nz;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(c % nx);
+    const long long r = c / nx;
+    const int y = (int)(r % ny), z = (int)(r / ny);
+    float nb = 0.f;
+    if (qa & 1u) nb += eps[c - x + (x == nx - 1 ? 0 : x + 1)] + eps[c - x + (x == 0 ? nx - 1 : x - 1)];
+    if (qa & 2u) {
+      const long long row = (long long)z * ny;
+      nb += eps[(row + (y == ny - 1 ? 0 : y + 1)) * nx + x] + eps[(row + (y == 0 ? ny - 1 : y - 1)) * nx + x];
+    }
+    if (qa & 4u) {
+      const long long pl = (long long)ny * nx;
+      nb += eps[(long long)(z == nz - 1 ? 0 : z + 1) * pl + (long long)y * nx + x] +
+            eps[(long long)(z == 0 ? nz - 1 : z - 1) * pl + (long long)y * nx + x];
+    }
+    sig[c] = __float2half_rn(fmaf(w0, eps[c], w1 * nb));
+  }
+}
+
+cudaError_t launch_shift(const LatticeDev &h, const float *eps, __half *sig, cudaStream_t s) {
+  const long long N = (long long)h.nx * h.ny * h.nz;
+  long long g = (N + 255) / 256;
+  if (g > 152LL * 32) g = 152LL * 32;
+  shift_kernel<<<(int)g, 256, 0, s>>>(eps, sig, h.nx, h.ny, h.nz, h.quad_axes, (float)h.qw0, (float)h.qw1);
+  return cudaGetLastError();
+}
+
 __global__ void f2d_kernel(const float *in, double *out, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)

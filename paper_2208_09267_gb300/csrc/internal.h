@@ -10,6 +10,7 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace lbm {
@@ -30,8 +31,8 @@ struct LatticeDev {
   void *pop;
   const void *eps;         // phi_ref (double for FP64, float otherwise)
   const void *deps;        // d_t phi or null
-  const float *sig_rd;     // shift the stored populations are encoded with
-  const float *sig_wr;     // shift the next write encodes with
+  const __half *sig_rd;    // shift sigma the stored populations are encoded with
+  const __half *sig_wr;    // shift the next write encodes with (from phi_ref)
   const void *force;       // 3*ncell, component-major, or null
   const void *dforce;
   double g[3];             // uniform force density
@@ -50,6 +51,8 @@ struct LatticeDev {
   int *status;             // device flag: nonzero after a bounded wait gave up
   unsigned wait_limit;     // iteration limit of the row kernel's stage waits
   int withhold_copies;     // test only: the row kernel issues no copies
+  int fp16_nearest;        // FP16 stores: 0 stochastic rounding, 1 nearest
+  int pad3;
 };
 
 constexpr int kRedWidth = 12;  // M0, mom x/y/z, |du|^2, |u|^2, nan, F x/y/z, spare x2
@@ -97,6 +100,11 @@ cudaError_t launch_init(const LatticeDev &host_mirror, const LatticeDev *L_dev, 
 // Decoded populations f[cell*Q + i] (double, natural order) into a device buffer.
 cudaError_t launch_get_populations(const LatticeDev &host_mirror, const LatticeDev *L_dev,
                                    long long n_host, double *f, cudaStream_t s);
+
+// Shift of the reduced-precision storages from phi_ref (float, N values):
+// sigma(x) = int phi dV by eq. (quad) on the lattice's quadrature axes,
+// rounded to half.
+cudaError_t launch_shift(const LatticeDev &host_mirror, const float *eps, __half *sig, cudaStream_t s);
 
 // Float -> double / double -> float conversions for field uploads.
 cudaError_t launch_convert_f2d(const float *in, double *out, long long n, cudaStream_t s);

@@ -38,6 +38,7 @@ struct lbm_vanse {
   long long N = 0;
   void *pop = nullptr;
   void *eps_buf[2] = {nullptr, nullptr};
+  __half *sig_buf[2] = {nullptr, nullptr};  // shift sigma of each phi_ref buffer
   int eps_cur = 0;
   void *deps = nullptr;
   void *force = nullptr, *dforce = nullptr;
@@ -126,6 +127,7 @@ static int validate_params(const lbm_vanse_params *p, std::string &why) {
     return 0;
   }
   if (p->kernel < 0 || p->kernel > 2) { why = "kernel must be 0, 1 or 2"; return 0; }
+  if (p->fp16_rounding < 0 || p->fp16_rounding > 1) { why = "fp16_rounding must be 0 or 1"; return 0; }
   if (p->kernel == 2 && p->storage == LBM_FP64) { why = "the row-staged kernel needs FP32 or FP16 storage"; return 0; }
   if (p->block_x < 0 || p->block_y < 0 || p->block_x * p->block_y > 256 ||
       (p->block_x > 0 && p->block_x % 32 != 0 && p->block_x * p->block_y % 32 != 0)) {
@@ -145,6 +147,7 @@ extern "C" size_t lbm_vanse_device_bytes(const lbm_vanse_params *p, int with_dep
   const size_t fe = p->storage == LBM_FP64 ? 8 : 4;
   size_t b = (size_t)Q * plane_of(N) * kElem[p->storage];  // populations
   b += 2 * (size_t)N * fe;                                  // phi double buffer
+  if (p->storage != LBM_FP64) b += 2 * (size_t)N * 2;       // shift double buffer
   if (with_deps) b += (size_t)N * fe;
   if (with_force_field) b += 2 * 3 * (size_t)N * fe;
   const lbm::StepLaunch ls = lbm::make_launch(p->nx, p->ny, p->nz, p->block_x, p->block_y);
@@ -181,8 +184,8 @@ extern "C" void lbm_vanse_destroy(lbm_vanse_t h) {
   if (!h) return;
   free_graphs(h);
   cudaStream_t s = h->stream;
-  void *ptrs[] = {h->pop, h->eps_buf[0], h->eps_buf[1], h->deps, h->force, h->dforce,
-                  h->u_prev, h->partials, h->stats_dev, h->status, h->d};
+  void *ptrs[] = {h->pop, h->eps_buf[0], h->eps_buf[1], h->sig_buf[0], h->sig_buf[1], h->deps, h->force,
+                  h->dforce, h->u_prev, h->partials, h->stats_dev, h->status, h->d};
   for (void *q : ptrs)
     if (q) cudaFreeAsync(q, s);
   if (h->stats_host) cudaFreeHost(h->stats_host);
@@ -238,6 +241,7 @@ extern "C" int lbm_vanse_create(const lbm_vanse_params *p, lbm_vanse_t *out) {
   m.cf = 1.0 - 0.5 / p->tau;
   m.rho0 = p->rho0;
   m.wait_limit = 1u << 22;
+  m.fp16_nearest = p->fp16_rounding == 1 ? 1 : 0;
   m.qw0 = lbm::quad_w0(qd);
   m.qw1 = lbm::quad_w1(qd);
   if (p->storage == LBM_FP16_SHIFTED) {
@@ -268,7 +272,9 @@ extern "C" int lbm_vanse_create(const lbm_vanse_params *p, lbm_vanse_t *out) {
       (rc = dev_alloc(h, (void **)&h->partials, (size_t)nblocks_alloc * lbm::kRedWidth * sizeof(double))) ||
       (rc = dev_alloc(h, (void **)&h->stats_dev, 64 * sizeof(double))) ||
       (rc = dev_alloc(h, (void **)&h->status, 64)) ||
-      (rc = dev_alloc(h, (void **)&h->d, sizeof(LatticeDev)))) {
+      (rc = dev_alloc(h, (void **)&h->d, sizeof(LatticeDev))) ||
+      (p->storage != LBM_FP64 && ((rc = dev_alloc(h, (void **)&h->sig_buf[0], (size_t)h->N * 2)) ||
+                                  (rc = dev_alloc(h, (void **)&h->sig_buf[1], (size_t)h->N * 2))))) {
     g_last_error = h->err;
     lbm_vanse_destroy(h);
     return rc;
@@ -301,7 +307,14 @@ extern "C" int lbm_vanse_create(const lbm_vanse_params *p, lbm_vanse_t *out) {
     return LBM_ECUDA;
   }
   h->eps_cur = 0;
-  m.sig_rd = m.sig_wr = p->storage == LBM_FP64 ? nullptr : static_cast<const float *>(h->eps_buf[0]);
+  m.sig_rd = m.sig_wr = h->sig_buf[0];
+  if (p->storage != LBM_FP64 &&
+      lbm::launch_shift(m, static_cast<const float *>(h->eps_buf[0]), h->sig_buf[0], h->stream) != cudaSuccess) {
+    fail(h, LBM_ECUDA, "shift kernel launch failed");
+    g_last_error = h->err;
+    lbm_vanse_destroy(h);
+    return LBM_ECUDA;
+  }
   if ((rc = push_mirror(h)) ||
       (rc = lbm::launch_init(h->h, h->d, 0, nullptr, nullptr, 0, h->stream) == cudaSuccess
                 ? LBM_OK
@@ -397,7 +410,9 @@ static int set_epsilon_any(lbm_vanse_t h, const void *eps, const void *deps, lon
   h->h.n_eps = n_ref;
   if (h->p.storage != LBM_FP64) {
     // the data stays encoded with the old shift until the next step
-    h->h.sig_wr = static_cast<const float *>(h->eps_buf[next]);
+    CUDA_TRY(h, lbm::launch_shift(h->h, static_cast<const float *>(h->eps_buf[next]), h->sig_buf[next],
+                                  h->stream));
+    h->h.sig_wr = h->sig_buf[next];
   }
   return push_mirror(h);
 }
@@ -778,7 +793,8 @@ extern "C" int lbm_vanse_save_state(lbm_vanse_t h, void *buf, size_t *size) {
   if (!h || !size) return fail(h, LBM_EINVAL, "NULL argument");
   const size_t pop_bytes = (size_t)h->Q * h->h.plane * kElem[h->p.storage];
   const size_t fb = (size_t)h->N * h->field_elem;
-  const size_t total = sizeof(StateHeader) + pop_bytes + 3 * fb + 6 * fb;
+  const size_t sb = h->p.storage == LBM_FP64 ? 0 : (size_t)h->N * 2;
+  const size_t total = sizeof(StateHeader) + pop_bytes + sb + 2 * fb + 6 * fb;
   if (!buf) {
     *size = total;
     return LBM_OK;
@@ -808,11 +824,10 @@ extern "C" int lbm_vanse_save_state(lbm_vanse_t h, void *buf, size_t *size) {
   CUDA_TRY(h, cudaMemcpyAsync(o, h->pop, pop_bytes, cudaMemcpyDeviceToHost, h->stream));
   o += pop_bytes;
   // phi (current), the shift the data is encoded with, d_t phi
-  const void *sig = h->p.storage == LBM_FP64 ? h->eps_buf[h->eps_cur] : (const void *)h->h.sig_rd;
   CUDA_TRY(h, cudaMemcpyAsync(o, h->eps_buf[h->eps_cur], fb, cudaMemcpyDeviceToHost, h->stream));
   o += fb;
-  CUDA_TRY(h, cudaMemcpyAsync(o, sig, fb, cudaMemcpyDeviceToHost, h->stream));
-  o += fb;
+  if (sb) CUDA_TRY(h, cudaMemcpyAsync(o, h->h.sig_rd, sb, cudaMemcpyDeviceToHost, h->stream));
+  o += sb;
   if (h->h.has_deps) CUDA_TRY(h, cudaMemcpyAsync(o, h->deps, fb, cudaMemcpyDeviceToHost, h->stream));
   o += fb;
   if (h->h.has_force) CUDA_TRY(h, cudaMemcpyAsync(o, h->force, 3 * fb, cudaMemcpyDeviceToHost, h->stream));
@@ -832,18 +847,20 @@ extern "C" int lbm_vanse_load_state(lbm_vanse_t h, const void *buf, size_t size)
   const size_t fb = (size_t)h->N * h->field_elem;
   if (memcmp(hd.magic, "LBMVANSE", 8) != 0 || hd.lattice != h->p.lattice || hd.storage != h->p.storage ||
       hd.nx != h->p.nx || hd.ny != h->p.ny || hd.nz != h->p.nz || hd.pop_bytes != pop_bytes ||
-      hd.field_bytes != fb || size < sizeof(StateHeader) + pop_bytes + 9 * fb)
+      hd.field_bytes != fb || size < sizeof(StateHeader) + pop_bytes + (h->p.storage == LBM_FP64 ? 0 : (size_t)h->N * 2) + 8 * fb)
     return fail(h, LBM_EINVAL, "state does not match this lattice");
   int rc;
   const char *o = static_cast<const char *>(buf) + sizeof(hd);
   CUDA_TRY(h, cudaMemcpyAsync(h->pop, o, pop_bytes, cudaMemcpyHostToDevice, h->stream));
   o += pop_bytes;
-  // the current phi goes to one buffer, the encoding shift to the other
+  // the current phi (and its shift) go to buffer 0; the shift the data is
+  // encoded with goes to shift buffer 1 when a shift change is pending
   const int cur = 0, other = 1;
+  const size_t sb = h->p.storage == LBM_FP64 ? 0 : (size_t)h->N * 2;
   CUDA_TRY(h, cudaMemcpyAsync(h->eps_buf[cur], o, fb, cudaMemcpyHostToDevice, h->stream));
   o += fb;
-  CUDA_TRY(h, cudaMemcpyAsync(h->eps_buf[other], o, fb, cudaMemcpyHostToDevice, h->stream));
-  o += fb;
+  if (sb) CUDA_TRY(h, cudaMemcpyAsync(h->sig_buf[other], o, sb, cudaMemcpyHostToDevice, h->stream));
+  o += sb;
   h->eps_cur = cur;
   if (hd.has_deps) {
     if (!h->deps && (rc = dev_alloc(h, &h->deps, fb))) return rc;
@@ -867,8 +884,10 @@ extern "C" int lbm_vanse_load_state(lbm_vanse_t h, const void *buf, size_t size)
   h->h.has_dforce = hd.has_dforce;
   for (int a = 0; a < 3; ++a) h->h.g[a] = hd.g[a];
   if (h->p.storage != LBM_FP64) {
-    h->h.sig_wr = static_cast<const float *>(h->eps_buf[cur]);
-    h->h.sig_rd = hd.reshift_pending ? static_cast<const float *>(h->eps_buf[other]) : h->h.sig_wr;
+    CUDA_TRY(h, lbm::launch_shift(h->h, static_cast<const float *>(h->eps_buf[cur]), h->sig_buf[cur],
+                                  h->stream));
+    h->h.sig_wr = h->sig_buf[cur];
+    h->h.sig_rd = hd.reshift_pending ? h->sig_buf[other] : h->h.sig_wr;
   }
   h->h.have_prev = 0;
   h->last_check_n = -1;

@@ -57,7 +57,7 @@ __device__ __forceinline__ double load_f(const LatticeDev &L, const SlotAddr &a,
   if (L.storage == 0) return static_cast<const double *>(L.pop)[off];
   double q = L.storage == 1 ? (double)static_cast<const float *>(L.pop)[off]
                             : (double)__half2float(static_cast<const __half *>(L.pop)[off]);
-  const double s = L.rho0 * (double)L.sig_rd[a.cell];
+  const double s = L.rho0 * (double)__half2float(L.sig_rd[a.cell]);
   return LAT::w(i) * (s + q * (double)L.inv_scale);
 }
 
@@ -69,7 +69,7 @@ __device__ __forceinline__ void store_f(const LatticeDev &L, int slot, long long
     static_cast<double *>(L.pop)[off] = f;
     return;
   }
-  const double s = L.rho0 * (double)L.sig_wr[cell];
+  const double s = L.rho0 * (double)__half2float(L.sig_wr[cell]);
   const double q = (f / LAT::w(i) - s) * (double)L.scale;
   if (L.storage == 1)
     static_cast<float *>(L.pop)[off] = (float)q;

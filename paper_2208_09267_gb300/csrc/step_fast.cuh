@@ -55,6 +55,47 @@ struct PopIO<__half> {
   static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
 };
 
+// Stochastic rounding of the FP16 stores.  A stored deviation can be many
+// times larger than its per-step change (a slowly accelerated flow changes
+// u by O(g) per step); round-to-nearest then drops the change every step, a
+// bias that accumulates.  Rounding up with probability equal to the
+// discarded fraction keeps every stored value unbiased.  The random bits
+// come from a counter-based generator keyed by (cell, time step), so runs
+// are reproducible and independent of how cells are grouped into launches.
+struct SRng {
+  unsigned s;
+  __device__ __forceinline__ explicit SRng(unsigned cell, long long n) {
+    unsigned x = cell * 0x9E3779B9u ^ (unsigned)n * 0x85EBCA6Bu ^ (unsigned)(n >> 32);
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    s = x;
+  }
+  // 13 random bits: the float mantissa bits that a half does not keep
+  __device__ __forceinline__ unsigned next13() {
+    s = s * 1664525u + 1013904223u;
+    return s >> 19;
+  }
+};
+
+// v rounded stochastically to half: add random bits below the half
+// mantissa to the float's magnitude, then truncate toward zero.
+__device__ __forceinline__ __half half_sr(float v, unsigned r13) {
+  return __float2half_rz(__uint_as_float(__float_as_uint(v) + r13));
+}
+
+template <class ST>
+__device__ __forceinline__ void store_pop(ST *p, float v, SRng &rng, bool sr) {
+  PopIO<ST>::st(p, v);
+}
+
+template <>
+__device__ __forceinline__ void store_pop<__half>(__half *p, float v, SRng &rng, bool sr) {
+  *p = sr ? half_sr(v, rng.next13()) : __float2half_rn(v);
+}
+
 struct Coords {
   int xs[3], ys[3], zs[3];  // coordinate of offset -1, 0, +1 (periodic)
   int nx, ny;
@@ -105,11 +146,11 @@ __device__ __forceinline__ void update_cell_fast(const LatticeDev &L, long long 
   const long long cell = C.at(0, 0, 0);
   const long long plane = L.plane;
   ST *__restrict__ pop = static_cast<ST *>(L.pop);
-  const float *__restrict__ srd = L.sig_rd;
-  const float *__restrict__ swr = L.sig_wr;
+  const __half *__restrict__ srd = L.sig_rd;
+  const __half *__restrict__ swr = L.sig_wr;
   const float rho0 = (float)L.rho0;
   const float inv_scale = L.inv_scale, scale = L.scale;
-  const float s_x = rho0 * __ldg(srd + cell);
+  const float s_x = rho0 * __half2float(srd[cell]);
 
   // 1. load and decode
   float d[Q];
@@ -125,7 +166,7 @@ __device__ __forceinline__ void update_cell_fast(const LatticeDev &L, long long 
     } else {
       const long long m = C.at(-cx, -cy, -cz);
       d[i] = fmaf(PopIO<ST>::ld(pop + (long long)opp_of(i) * plane + m), inv_scale,
-                  fmaf(rho0, __ldg(srd + m), -s_x));
+                  fmaf(rho0, __half2float(srd[m]), -s_x));
     }
   }
 
@@ -230,6 +271,8 @@ __device__ __forceinline__ void update_cell_fast(const LatticeDev &L, long long 
   // 7. collide (deviation form) and 8. stream
   const float omega = (float)L.omega, cf = (float)L.cf;
   const bool reshift = srd != swr;
+  SRng rng((unsigned)cell, n);
+  const bool sr = L.fp16_nearest == 0;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int cx = LAT::c(i, 0), cy = LAT::c(i, 1), cz = LAT::c(i, 2);
@@ -248,20 +291,20 @@ __device__ __forceinline__ void update_cell_fast(const LatticeDev &L, long long 
     // as the decode does, so that a stored value round-trips
     if (!ODD) {
       float q = ds;
-      if (reshift) q += fmaf(-rho0, __ldg(swr + cell), s_x);
-      PopIO<ST>::st(pop + (long long)opp_of(i) * plane + cell, q * scale);
+      if (reshift) q += fmaf(-rho0, __half2float(swr[cell]), s_x);
+      store_pop<ST>(pop + (long long)opp_of(i) * plane + cell, q * scale, rng, sr);
     } else if (i == 0) {
       float q = ds;
-      if (reshift) q += fmaf(-rho0, __ldg(swr + cell), s_x);
-      PopIO<ST>::st(pop + cell, q * scale);
+      if (reshift) q += fmaf(-rho0, __half2float(swr[cell]), s_x);
+      store_pop<ST>(pop + cell, q * scale, rng, sr);
     } else if (walls && solid_at(walls, x, y, z, cx, cy, cz, nx, ny, nz)) {
       float q = ds;
-      if (reshift) q += fmaf(-rho0, __ldg(swr + cell), s_x);
-      PopIO<ST>::st(pop + (long long)opp_of(i) * plane + cell, q * scale);
+      if (reshift) q += fmaf(-rho0, __half2float(swr[cell]), s_x);
+      store_pop<ST>(pop + (long long)opp_of(i) * plane + cell, q * scale, rng, sr);
     } else {
       const long long m = C.at(cx, cy, cz);
-      const float q = ds + fmaf(-rho0, __ldg(swr + m), s_x);
-      PopIO<ST>::st(pop + (long long)i * plane + m, q * scale);
+      const float q = ds + fmaf(-rho0, __half2float(swr[m]), s_x);
+      store_pop<ST>(pop + (long long)i * plane + m, q * scale, rng, sr);
     }
   }
 }

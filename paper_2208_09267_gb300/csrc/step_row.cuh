@@ -85,32 +85,35 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsig
 
 // Shared-memory layout of one stage.  Rows are stored at a compile-time
 // pitch (PITCH elements >= nx) so that every shared-memory address below is
-// a register plus an immediate.
+// a register plus an immediate.  Order: Q population rows, the shift rows
+// (half; the 3x3 block of rows (y+dy, z+dz) at odd steps, the own row at even
+// steps), the phi_ref rows of the 5-point cross and the d_t phi rows of the
+// cross (2D: the 3 rows y-1, y, y+1).
 template <class LAT, class ST, bool ODD, int PITCH>
 struct RowLayout {
-  static constexpr int kEpsRows = LAT::D == 2 ? 3 : (ODD ? 9 : 5);
-  static constexpr int kDepsRows = LAT::D == 2 ? 3 : 5;
+  static constexpr int kSigRows = ODD ? (LAT::D == 2 ? 3 : 9) : 1;
+  static constexpr int kEpsRows = LAT::D == 2 ? 3 : 5;
+  static constexpr int kDepsRows = kEpsRows;
   static constexpr int kPopBytes = PITCH * (int)sizeof(ST);
+  static constexpr int kSigBytes = PITCH * 2;
   static constexpr int kRowBytes = PITCH * 4;
-  static constexpr int kEpsOff = LAT::Q * kPopBytes;
+  static constexpr int kSigOff = LAT::Q * kPopBytes;
+  static constexpr int kEpsOff = kSigOff + kSigRows * kSigBytes;
   static constexpr int kDepsOff = kEpsOff + kEpsRows * kRowBytes;
   static constexpr int kStageBytes = kDepsOff + kDepsRows * kRowBytes;
-  static constexpr int kCopiesMax = LAT::Q + kEpsRows + kDepsRows;
 };
 
-// Index of the phi_ref row (dy, dz) inside a stage: 3x3 block at odd steps
-// (3D), 5-point cross at even steps (3D), 3 rows in 2D.
-template <class LAT, bool ODD>
-__host__ __device__ constexpr int eps_row_index(int dy, int dz) {
-  return LAT::D == 2 ? dy + 1
-                     : (ODD ? (dz + 1) * 3 + (dy + 1)
-                            : (dz == 0 ? (dy == 0 ? 0 : (dy < 0 ? 1 : 2)) : (dz < 0 ? 3 : 4)));
+// Row (dy, dz) of the 5-point cross: 0 centre, 1 y-1, 2 y+1, 3 z-1, 4 z+1
+// (2D: dy + 1).
+template <class LAT>
+__host__ __device__ constexpr int cross_index(int dy, int dz) {
+  return LAT::D == 2 ? dy + 1 : (dz == 0 ? (dy == 0 ? 0 : (dy < 0 ? 1 : 2)) : (dz < 0 ? 3 : 4));
 }
 
-// Index of the d_t phi row (dy, dz): 5-point cross (3D), 3 rows (2D).
-template <class LAT>
-__host__ __device__ constexpr int deps_row_index(int dy, int dz) {
-  return LAT::D == 2 ? dy + 1 : (dz == 0 ? (dy == 0 ? 0 : (dy < 0 ? 1 : 2)) : (dz < 0 ? 3 : 4));
+// Shift row (dy, dz): 3x3 block at odd steps (2D: dy + 1), own row at even.
+template <class LAT, bool ODD>
+__host__ __device__ constexpr int sig_index(int dy, int dz) {
+  return ODD ? (LAT::D == 2 ? dy + 1 : (dz + 1) * 3 + (dy + 1)) : 0;
 }
 
 __device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
@@ -135,7 +138,7 @@ __device__ __forceinline__ RowCtx make_row_ctx(const LatticeDev &L, int y, int z
   return c;
 }
 
-// Warp 0: issue every bulk copy of a row into `stage`, one copy per lane.
+// Producer warp: issue every bulk copy of a row into `stage`, one per lane.
 template <class LAT, class ST, bool ODD, int PITCH>
 __device__ __forceinline__ void issue_row(const LatticeDev &L, unsigned char *stage, unsigned long long *bar,
                                           const RowCtx &rc) {
@@ -143,14 +146,19 @@ __device__ __forceinline__ void issue_row(const LatticeDev &L, unsigned char *st
   const int lane = threadIdx.x & 31;
   const bool tv = L.has_deps != 0;
   const int nx = L.nx;
-  const unsigned pbytes = (unsigned)nx * (unsigned)sizeof(ST), rbytes = (unsigned)nx * 4u;
-  const int ncopies = LAT::Q + Lay::kEpsRows + (tv ? Lay::kDepsRows : 0);
+  const unsigned pbytes = (unsigned)nx * (unsigned)sizeof(ST), sbytes = (unsigned)nx * 2u,
+                 rbytes = (unsigned)nx * 4u;
+  const int nfield = Lay::kEpsRows + (tv ? Lay::kDepsRows : 0);
+  const int ncopies = LAT::Q + Lay::kSigRows + nfield;
   if (lane == 0)
-    mbar_arrive_expect_tx(bar, (unsigned)LAT::Q * pbytes + (unsigned)(ncopies - LAT::Q) * rbytes);
+    mbar_arrive_expect_tx(bar, (unsigned)LAT::Q * pbytes + (unsigned)Lay::kSigRows * sbytes +
+                                   (unsigned)nfield * rbytes);
   __syncwarp();
   const ST *pop = static_cast<const ST *>(L.pop);
+  const __half *sig = L.sig_wr;
   const float *eps = static_cast<const float *>(L.eps);
   const float *deps = static_cast<const float *>(L.deps);
+  const int dys[5] = {0, -1, 1, 0, 0}, dzs[5] = {0, 0, 0, -1, 1};
   for (int j = lane; j < ncopies; j += 32) {
     if (j < LAT::Q) {
       const int i = j;
@@ -165,33 +173,22 @@ __device__ __forceinline__ void issue_row(const LatticeDev &L, unsigned char *st
       }
       const ST *src = pop + (long long)plane_i * L.plane + rc.base[dz + 1][dy + 1];
       bulk_g2s(stage + i * Lay::kPopBytes, src, pbytes, bar);
-    } else if (j < LAT::Q + Lay::kEpsRows) {
+    } else if (j < LAT::Q + Lay::kSigRows) {
       const int e = j - LAT::Q;
-      int dy, dz;
-      if (LAT::D == 2) {
-        dy = e - 1;
-        dz = 0;
-      } else if (ODD) {
-        dy = e % 3 - 1;
-        dz = e / 3 - 1;
-      } else {
-        const int dys[5] = {0, -1, 1, 0, 0}, dzs[5] = {0, 0, 0, -1, 1};
-        dy = dys[e];
-        dz = dzs[e];
+      int dy = 0, dz = 0;
+      if (ODD) {
+        dy = (LAT::D == 2 ? e : e % 3) - 1;
+        dz = LAT::D == 2 ? 0 : e / 3 - 1;
       }
-      bulk_g2s(stage + Lay::kEpsOff + e * Lay::kRowBytes, eps + rc.base[dz + 1][dy + 1], rbytes, bar);
+      bulk_g2s(stage + Lay::kSigOff + e * Lay::kSigBytes, sig + rc.base[dz + 1][dy + 1], sbytes, bar);
     } else {
-      const int e = j - LAT::Q - Lay::kEpsRows;
-      int dy, dz;
-      if (LAT::D == 2) {
-        dy = e - 1;
-        dz = 0;
-      } else {
-        const int dys[5] = {0, -1, 1, 0, 0}, dzs[5] = {0, 0, 0, -1, 1};
-        dy = dys[e];
-        dz = dzs[e];
-      }
-      bulk_g2s(stage + Lay::kDepsOff + e * Lay::kRowBytes, deps + rc.base[dz + 1][dy + 1], rbytes, bar);
+      const int f = j - LAT::Q - Lay::kSigRows;
+      const int e = f % Lay::kEpsRows;
+      const int dy = LAT::D == 2 ? e - 1 : dys[e], dz = LAT::D == 2 ? 0 : dzs[e];
+      if (f < Lay::kEpsRows)
+        bulk_g2s(stage + Lay::kEpsOff + e * Lay::kRowBytes, eps + rc.base[dz + 1][dy + 1], rbytes, bar);
+      else
+        bulk_g2s(stage + Lay::kDepsOff + e * Lay::kRowBytes, deps + rc.base[dz + 1][dy + 1], rbytes, bar);
     }
   }
 }
@@ -206,14 +203,15 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
   constexpr bool kScaled = sizeof(ST) < 4;  // FP16 stores deviations times 2^k
   const int nx = L.nx;
   const ST *prow = reinterpret_cast<const ST *>(stage);
+  const __half *srow = reinterpret_cast<const __half *>(stage + Lay::kSigOff);
   const float *erow = reinterpret_cast<const float *>(stage + Lay::kEpsOff);
   const float *drow = reinterpret_cast<const float *>(stage + Lay::kDepsOff);
   const bool tv = L.has_deps != 0;
   const float dn = (float)(n - L.n_eps);
   const float rho0 = (float)L.rho0;
   const float inv_scale = L.inv_scale, scale = L.scale;
-  const float *__restrict__ srd = L.sig_rd;
-  const bool reshift = srd != static_cast<const float *>(L.eps);
+  const __half *__restrict__ srd = L.sig_rd;
+  const bool reshift = srd != L.sig_wr;  // shift changed by the last set_epsilon
   ST *__restrict__ pop = static_cast<ST *>(L.pop);
   const int plane = (int)L.plane;
   const float omega = (float)L.omega;
@@ -221,8 +219,9 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
   const float cf3 = 3.0f * (float)L.cf, cf9 = 9.0f * (float)L.cf;
   const unsigned qa = L.quad_axes;
 
-#define EPS_AT(dy, dz, xx) erow[eps_row_index<LAT, ODD>((dy), (dz)) * PITCH + (xx)]
-#define DEPS_AT(dy, dz, xx) drow[deps_row_index<LAT>((dy), (dz)) * PITCH + (xx)]
+#define EPS_AT(dy, dz, xx) erow[cross_index<LAT>((dy), (dz)) * PITCH + (xx)]
+#define DEPS_AT(dy, dz, xx) drow[cross_index<LAT>((dy), (dz)) * PITCH + (xx)]
+#define SIG_AT(dy, dz, xx) __half2float(srow[sig_index<LAT, ODD>((dy), (dz)) * PITCH + (xx)])
   // slot of population i read from / written to this cell's own memory?
 #define OWN_SRC(i) (!ODD || (i) == 0 || (WALLS && ((rc.solid >> ((1 - LAT::c((i), 2)) * 3 + (1 - LAT::c((i), 1)))) & 1u)))
 #define OWN_DST(i) (!ODD || (i) == 0 || (WALLS && ((rc.solid >> ((1 + LAT::c((i), 2)) * 3 + (1 + LAT::c((i), 1)))) & 1u)))
@@ -230,8 +229,9 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
   const int xs[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};
   const int cell = rc.base[1][1] + x;
   const float e_own = EPS_AT(0, 0, x);
+  const float sig_own = SIG_AT(0, 0, x);  // sigma_wr of this cell
   // the cell's frame: its own shift as stored (sigma_rd)
-  const float s_x = rho0 * (reshift ? __ldg(srd + cell) : e_own);
+  const float s_x = rho0 * (reshift ? __half2float(srd[cell]) : sig_own);
 
   // 1. decode: d_i = f_i/w_i - s_x.  A value stored in another cell m carries
   //    that cell's shift: add delta_i = rho0 sigma(m) - s_x (exact product in
@@ -248,7 +248,8 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
       delta[i] = 0.f;
       d[i] = qs;
     } else {
-      const float sm = reshift ? __ldg(srd + rc.base[1 - cz][1 - cy] + xs[1 - cx]) : EPS_AT(-cy, -cz, xs[1 - cx]);
+      const float sm =
+          reshift ? __half2float(srd[rc.base[1 - cz][1 - cy] + xs[1 - cx]]) : SIG_AT(-cy, -cz, xs[1 - cx]);
       delta[i] = fmaf(rho0, sm, -s_x);
       d[i] = qs + delta[i];
     }
@@ -353,9 +354,33 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
   //   direction.
   const float m15usq = -1.5f * usq;
   const float m3uF = -cf3 * uF;
-  const float enc_own = reshift ? fmaf(-rho0, e_own, s_x) : 0.f;
+  const float enc_own = reshift ? fmaf(-rho0, sig_own, s_x) : 0.f;
+  SRng rng((unsigned)cell, n);
+  const bool sr = L.fp16_nearest == 0;
+  auto store = [&](int i, float dstar) {
+    const int cx = LAT::c(i, 0), cy = LAT::c(i, 1), cz = LAT::c(i, 2);
+    if (OWN_DST(i)) {
+      const float v = dstar + enc_own;
+      store_pop<ST>(pop + opp_of(i) * plane + cell, kScaled ? v * scale : v, rng, sr);
+    } else {
+      const int xm = xs[1 + cx];
+      float enc;
+      if (!reshift && !OWN_SRC(opp_of(i)))
+        enc = -delta[opp_of(i)];
+      else
+        enc = fmaf(-rho0, SIG_AT(cy, cz, xm), s_x);
+      const float v = dstar + enc;
+      store_pop<ST>(pop + i * plane + rc.base[1 + cz][1 + cy] + xm, kScaled ? v * scale : v, rng, sr);
+    }
+  };
+  // rest population: cu = cF = 0
+  store(0, fmaf(om1, d[0], fmaf(omega, fmaf(M0, m15usq, dM), m3uF)));
+  // opposite pairs (i, i+1): cu and cF change sign, so
+  //   omega d^eq + Omega = A +- B,  A = omega (dM + M0 (4.5 cu^2 - 1.5 u.u)) + cf (9 cu cF - 3 u.F),
+  //                                 B = 3 omega M0 cu + 3 cf cF
+  const float oM03 = 3.0f * omega * M0;
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
+  for (int i = 1; i < Q; i += 2) {
     const int cx = LAT::c(i, 0), cy = LAT::c(i, 1), cz = LAT::c(i, 2);
     float cu = 0.f, cF = 0.f;
     if (cx == 1) { cu += u0; cF += F0; }
@@ -364,26 +389,15 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
     if (cy == -1) { cu -= u1; cF -= F1; }
     if (cz == 1) { cu += u2; cF += F2; }
     if (cz == -1) { cu -= u2; cF -= F2; }
-    const float pm1 = fmaf(cu, fmaf(4.5f, cu, 3.0f), m15usq);
-    const float deq = fmaf(M0, pm1, dM);
-    const float src = fmaf(cu * cf9, cF, fmaf(cf3, cF, m3uF));
-    const float dstar = fmaf(om1, d[i], fmaf(omega, deq, src));
-    if (OWN_DST(i)) {
-      const float v = dstar + enc_own;
-      PopIO<ST>::st(pop + opp_of(i) * plane + cell, kScaled ? v * scale : v);
-    } else {
-      const int xm = xs[1 + cx];
-      float enc;
-      if (!reshift && !OWN_SRC(opp_of(i)))
-        enc = -delta[opp_of(i)];
-      else
-        enc = fmaf(-rho0, EPS_AT(cy, cz, xm), s_x);
-      const float v = dstar + enc;
-      PopIO<ST>::st(pop + i * plane + rc.base[1 + cz][1 + cy] + xm, kScaled ? v * scale : v);
-    }
+    const float t = fmaf(M0, fmaf(4.5f * cu, cu, m15usq), dM);
+    const float A = fmaf(omega, t, fmaf(cf9 * cu, cF, m3uF));
+    const float B = fmaf(oM03, cu, cf3 * cF);
+    store(i, fmaf(om1, d[i], A + B));
+    store(i + 1, fmaf(om1, d[i + 1], A - B));
   }
 #undef EPS_AT
 #undef DEPS_AT
+#undef SIG_AT
 #undef OWN_SRC
 #undef OWN_DST
 }
@@ -508,8 +522,11 @@ namespace lbm {
 // Host side: launch and planning of the row kernel for one lattice type.
 // ls.row encodes the variant: bit 0 set = in use, bit 1 = walls, bit 2 =
 // pitch 512 (else 256).
+#ifndef LBM_ROW_NSTAGE_256
+#define LBM_ROW_NSTAGE_256 3
+#endif
 template <int P>
-constexpr int row_stages() { return P <= 256 ? 3 : 2; }
+constexpr int row_stages() { return P <= 256 ? LBM_ROW_NSTAGE_256 : 2; }
 
 template <class LAT, class ST, bool W, int P, int MINB>
 cudaError_t launch_row_v(const LatticeDev *L_dev, bool odd, int red, int k, const StepLaunch &ls,

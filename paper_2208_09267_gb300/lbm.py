@@ -41,6 +41,7 @@ class Params(ctypes.Structure):
         ("walls", ctypes.c_uint), ("fp16_scale_log2", ctypes.c_int),
         ("cuda_stream", ctypes.c_void_p), ("hbm_budget_bytes", ctypes.c_size_t),
         ("block_x", ctypes.c_int), ("block_y", ctypes.c_int), ("kernel", ctypes.c_int),
+        ("fp16_rounding", ctypes.c_int),
     ]
 
 
@@ -172,7 +173,7 @@ class Lattice:
 
     def __init__(self, lattice="D3Q19", shape=(32, 32, 32), tau=0.6, storage="fp32", rho0=1.0,
                  quad_axes=0, quad_dim=0, walls=0, fp16_scale_log2=10, stream=None,
-                 hbm_budget_bytes=0, block=(0, 0), kernel=0):
+                 hbm_budget_bytes=0, block=(0, 0), kernel=0, fp16_rounding="stochastic"):
         """shape is (nx, ny, nz); nz = 1 for D2Q9."""
         L = lib()
         p = Params()
@@ -188,6 +189,7 @@ class Lattice:
         p.hbm_budget_bytes = int(hbm_budget_bytes)
         p.block_x, p.block_y = int(block[0]), int(block[1])
         p.kernel = {"auto": 0, "cell": 1, "row": 2}.get(kernel, kernel)
+        p.fp16_rounding = {"stochastic": 0, "nearest": 1}.get(fp16_rounding, fp16_rounding)
         h = ctypes.c_void_p()
         _check(L.lbm_vanse_create(ctypes.byref(p), ctypes.byref(h)))
         self._h = h
