@@ -97,7 +97,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -219,8 +219,10 @@ def run_gpu(args, rank, world):
         st = lat.step(1)  # one check step (not timed) to confirm the run is sane
         if st["nan_seen"]:
             raise RuntimeError(f"{storage}: NaN after the timed steps")
+        kname = "step_row_kernel" if lat.row_kernel else "step_fast_kernel"
         results[storage] = {"total_ms": total_ms, "kernel_ms": step_ms / nk, "launches": launches,
-                            "clocks": clk.summary(), "mass": st["mass"]}
+                            "clocks": clk.summary(), "mass": st["mass"],
+                            "kernel": f"{kname}<D3Q19,{'float' if storage == 'fp32' else '__half'}>"}
         lat.close()
 
     # end to end through the C ABI with host buffers (FP32)
@@ -371,7 +373,7 @@ def cpu_baseline(sample_L=48, steps=None, budget_s=20.0):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--size", type=int, default=L_DEFAULT)
@@ -433,7 +435,7 @@ def main():
                      "frac": achieved / peak, "peak_kind": f"{peak_kind} copy bandwidth",
                      "traffic": profiled_traffic(main_st, src_hash),
                      "algorithmic_bytes_per_cell": bpc,
-                     "kernel": "step_fast_kernel<D3Q19,float>", "kernel_ms": r["kernel_ms"]},
+                     "kernel": r["kernel"], "kernel_ms": r["kernel_ms"]},
         "gpu_launches": r["launches"], "clocks": r["clocks"], "e2e": e2e,
     }
     for st, rr in res.items():

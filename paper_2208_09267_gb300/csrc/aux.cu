@@ -140,6 +140,28 @@ cudaError_t launch_shift(const LatticeDev &h, const float *eps, __half *sig, cud
   return cudaGetLastError();
 }
 
+template <class T>
+__global__ void validate_kernel(const T *data, long long n, int unit, long long *first_bad) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double v = (double)data[i];
+    const bool bad = !isfinite(v) || (unit && !(v > 0.0 && v <= 1.0));
+    if (bad) atomicMin((unsigned long long *)first_bad, (unsigned long long)i);
+  }
+}
+
+cudaError_t launch_validate(const void *data, long long n, int is_f64, int unit, long long *first_bad,
+                            cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  long long g = (n + 255) / 256;
+  if (g > 152LL * 16) g = 152LL * 16;
+  if (is_f64)
+    validate_kernel<double><<<(int)g, 256, 0, s>>>(static_cast<const double *>(data), n, unit, first_bad);
+  else
+    validate_kernel<float><<<(int)g, 256, 0, s>>>(static_cast<const float *>(data), n, unit, first_bad);
+  return cudaGetLastError();
+}
+
 __global__ void f2d_kernel(const float *in, double *out, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)

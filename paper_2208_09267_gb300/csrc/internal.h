@@ -106,6 +106,12 @@ cudaError_t launch_get_populations(const LatticeDev &host_mirror, const LatticeD
 // rounded to half.
 cudaError_t launch_shift(const LatticeDev &host_mirror, const float *eps, __half *sig, cudaStream_t s);
 
+// Scan n values (float or double) on the device: sets *first_bad to the
+// smallest index whose value is not finite or, with unit != 0, not in (0, 1].
+// *first_bad must hold a value >= n beforehand.
+cudaError_t launch_validate(const void *data, long long n, int is_f64, int unit, long long *first_bad,
+                            cudaStream_t s);
+
 // Float -> double / double -> float conversions for field uploads.
 cudaError_t launch_convert_f2d(const float *in, double *out, long long n, cudaStream_t s);
 cudaError_t launch_convert_d2f(const double *in, float *out, long long n, cudaStream_t s);

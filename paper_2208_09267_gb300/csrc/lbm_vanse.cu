@@ -383,25 +383,38 @@ static int check_host_values(lbm_vanse_t h, const T *v, long long n, bool unit_i
   return LBM_OK;
 }
 
+// Check an uploaded copy of host values on the device (one scan kernel and a
+// readback of the first bad index); synchronises the stream.
+static int check_uploaded(lbm_vanse_t h, const void *dev, long long n, int is_f64, bool unit_interval,
+                          const char *what) {
+  long long *flag = reinterpret_cast<long long *>(h->stats_dev + 48);
+  long long *host = reinterpret_cast<long long *>(h->stats_host + 48);
+  const long long none = n;
+  CUDA_TRY(h, cudaMemcpyAsync(flag, &none, sizeof(none), cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, lbm::launch_validate(dev, n, is_f64, unit_interval ? 1 : 0, flag, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(host, flag, sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  if (*host < n)
+    return fail(h, LBM_EINVAL, "%s[%lld] is %s", what, *host,
+                unit_interval ? "not finite or outside (0, 1]" : "not finite");
+  return LBM_OK;
+}
+
 static int set_epsilon_any(lbm_vanse_t h, const void *eps, const void *deps, long long n_ref,
                            int on_device, int is_f64) {
   if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
   if (!eps) return fail(h, LBM_EINVAL, "eps_ref is NULL");
   int rc;
-  if (!on_device) {
-    if (is_f64) {
-      if ((rc = check_host_values(h, static_cast<const double *>(eps), h->N, true, "eps_ref"))) return rc;
-      if (deps && (rc = check_host_values(h, static_cast<const double *>(deps), h->N, false, "deps_dt"))) return rc;
-    } else {
-      if ((rc = check_host_values(h, static_cast<const float *>(eps), h->N, true, "eps_ref"))) return rc;
-      if (deps && (rc = check_host_values(h, static_cast<const float *>(deps), h->N, false, "deps_dt"))) return rc;
-    }
-  }
   const int next = 1 - h->eps_cur;
+  const int dev_f64 = h->field_elem == 8;
+  // host values are checked on the device after the upload; nothing of the
+  // handle's state changes before both fields passed
   if ((rc = upload_field(h, h->eps_buf[next], eps, h->N, is_f64, on_device))) return rc;
+  if (!on_device && (rc = check_uploaded(h, h->eps_buf[next], h->N, dev_f64, true, "eps_ref"))) return rc;
   if (deps) {
     if (!h->deps && (rc = dev_alloc(h, &h->deps, (size_t)h->N * h->field_elem))) return rc;
     if ((rc = upload_field(h, h->deps, deps, h->N, is_f64, on_device))) return rc;
+    if (!on_device && (rc = check_uploaded(h, h->deps, h->N, dev_f64, false, "deps_dt"))) return rc;
     h->h.has_deps = 1;
   } else {
     h->h.has_deps = 0;

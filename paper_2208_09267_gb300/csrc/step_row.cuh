@@ -138,7 +138,33 @@ __device__ __forceinline__ RowCtx make_row_ctx(const LatticeDev &L, int y, int z
   return c;
 }
 
-// Producer warp: issue every bulk copy of a row into `stage`, one per lane.
+// Offsets (dy, dz) of the 5-point cross rows (2D: e - 1, 0).
+template <class LAT>
+__host__ __device__ constexpr int cross_dy(int e) {
+  return LAT::D == 2 ? e - 1 : (e == 1 ? -1 : (e == 2 ? 1 : 0));
+}
+template <class LAT>
+__host__ __device__ constexpr int cross_dz(int e) {
+  return LAT::D == 2 ? 0 : (e == 3 ? -1 : (e == 4 ? 1 : 0));
+}
+
+// (c_iy, c_iz) of direction i (runtime i), by unrolled selects: no table in
+// local memory.
+template <class LAT>
+__device__ __forceinline__ void dir_yz(int i, int &cy, int &cz) {
+  cy = 0;
+  cz = 0;
+#pragma unroll
+  for (int k = 1; k < LAT::Q; ++k) {
+    const bool hit = k == i;
+    cy = hit ? LAT::c(k, 1) : cy;
+    cz = hit ? LAT::c(k, 2) : cz;
+  }
+}
+
+// Producer warp: issue every bulk copy of a row into `stage`.  Copy j is
+// issued by lane j % 32; each lane computes its copy's source, destination
+// and size, then the whole warp issues one cp.async.bulk per round.
 template <class LAT, class ST, bool ODD, int PITCH>
 __device__ __forceinline__ void issue_row(const LatticeDev &L, unsigned char *stage, unsigned long long *bar,
                                           const RowCtx &rc) {
@@ -154,42 +180,43 @@ __device__ __forceinline__ void issue_row(const LatticeDev &L, unsigned char *st
     mbar_arrive_expect_tx(bar, (unsigned)LAT::Q * pbytes + (unsigned)Lay::kSigRows * sbytes +
                                    (unsigned)nfield * rbytes);
   __syncwarp();
-  const ST *pop = static_cast<const ST *>(L.pop);
-  const __half *sig = L.sig_wr;
-  const float *eps = static_cast<const float *>(L.eps);
-  const float *deps = static_cast<const float *>(L.deps);
-  const int dys[5] = {0, -1, 1, 0, 0}, dzs[5] = {0, 0, 0, -1, 1};
+  const char *pop = static_cast<const char *>(L.pop);
+  const long long plane_bytes = L.plane * (long long)sizeof(ST);
+  const unsigned solid = rc.solid;
   for (int j = lane; j < ncopies; j += 32) {
+    const char *src;
+    unsigned char *dst;
+    unsigned bytes;
     if (j < LAT::Q) {
-      const int i = j;
-      int plane_i = i, dy = 0, dz = 0;
-      if (ODD && i != 0) {
-        const int cy = LAT::c(i, 1), cz = LAT::c(i, 2);
-        if (!((rc.solid >> ((1 - cz) * 3 + (1 - cy))) & 1u)) {
-          plane_i = opp_of(i);
-          dy = -cy;
-          dz = -cz;
-        }
+      int cy, cz;
+      dir_yz<LAT>(j, cy, cz);
+      int plane_i = j, dy = 0, dz = 0;
+      if (ODD && j != 0 && !((solid >> ((1 - cz) * 3 + (1 - cy))) & 1u)) {
+        plane_i = opp_of(j);
+        dy = -cy;
+        dz = -cz;
       }
-      const ST *src = pop + (long long)plane_i * L.plane + rc.base[dz + 1][dy + 1];
-      bulk_g2s(stage + i * Lay::kPopBytes, src, pbytes, bar);
+      src = pop + plane_i * plane_bytes + (long long)rc.base[dz + 1][dy + 1] * (long long)sizeof(ST);
+      dst = stage + j * Lay::kPopBytes;
+      bytes = pbytes;
     } else if (j < LAT::Q + Lay::kSigRows) {
       const int e = j - LAT::Q;
-      int dy = 0, dz = 0;
-      if (ODD) {
-        dy = (LAT::D == 2 ? e : e % 3) - 1;
-        dz = LAT::D == 2 ? 0 : e / 3 - 1;
-      }
-      bulk_g2s(stage + Lay::kSigOff + e * Lay::kSigBytes, sig + rc.base[dz + 1][dy + 1], sbytes, bar);
+      const int dy = ODD ? (LAT::D == 2 ? e : e % 3) - 1 : 0;
+      const int dz = ODD ? (LAT::D == 2 ? 0 : e / 3 - 1) : 0;
+      src = reinterpret_cast<const char *>(L.sig_wr + rc.base[dz + 1][dy + 1]);
+      dst = stage + Lay::kSigOff + e * Lay::kSigBytes;
+      bytes = sbytes;
     } else {
       const int f = j - LAT::Q - Lay::kSigRows;
-      const int e = f % Lay::kEpsRows;
-      const int dy = LAT::D == 2 ? e - 1 : dys[e], dz = LAT::D == 2 ? 0 : dzs[e];
-      if (f < Lay::kEpsRows)
-        bulk_g2s(stage + Lay::kEpsOff + e * Lay::kRowBytes, eps + rc.base[dz + 1][dy + 1], rbytes, bar);
-      else
-        bulk_g2s(stage + Lay::kDepsOff + e * Lay::kRowBytes, deps + rc.base[dz + 1][dy + 1], rbytes, bar);
+      const bool is_deps = f >= Lay::kEpsRows;
+      const int e = is_deps ? f - Lay::kEpsRows : f;
+      const int off = rc.base[cross_dz<LAT>(e) + 1][cross_dy<LAT>(e) + 1];
+      const float *base = static_cast<const float *>(is_deps ? L.deps : L.eps);
+      src = reinterpret_cast<const char *>(base + off);
+      dst = stage + (is_deps ? Lay::kDepsOff : Lay::kEpsOff) + e * Lay::kRowBytes;
+      bytes = rbytes;
     }
+    bulk_g2s(dst, src, bytes, bar);
   }
 }
 
@@ -357,24 +384,28 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
   const float enc_own = reshift ? fmaf(-rho0, sig_own, s_x) : 0.f;
   SRng rng((unsigned)cell, n);
   const bool sr = L.fp16_nearest == 0;
-  auto store = [&](int i, float dstar) {
-    const int cx = LAT::c(i, 0), cy = LAT::c(i, 1), cz = LAT::c(i, 2);
-    if (OWN_DST(i)) {
-      const float v = dstar + enc_own;
-      store_pop<ST>(pop + opp_of(i) * plane + cell, kScaled ? v * scale : v, rng, sr);
-    } else {
-      const int xm = xs[1 + cx];
-      float enc;
-      if (!reshift && !OWN_SRC(opp_of(i)))
-        enc = -delta[opp_of(i)];
-      else
-        enc = fmaf(-rho0, SIG_AT(cy, cz, xm), s_x);
-      const float v = dstar + enc;
-      store_pop<ST>(pop + i * plane + rc.base[1 + cz][1 + cy] + xm, kScaled ? v * scale : v, rng, sr);
-    }
-  };
+  // store population i (compile-time index) with post-collision deviation DSTAR
+#define STORE_POP(i, DSTAR)                                                                        \
+  do {                                                                                             \
+    const int cx_ = LAT::c((i), 0), cy_ = LAT::c((i), 1), cz_ = LAT::c((i), 2);                    \
+    const float ds_ = (DSTAR);                                                                     \
+    if (OWN_DST(i)) {                                                                              \
+      const float v_ = ds_ + enc_own;                                                              \
+      store_pop<ST>(pop + opp_of(i) * plane + cell, kScaled ? v_ * scale : v_, rng, sr);           \
+    } else {                                                                                       \
+      const int xm_ = xs[1 + cx_];                                                                 \
+      float enc_;                                                                                  \
+      if (!reshift && !OWN_SRC(opp_of(i)))                                                         \
+        enc_ = -delta[opp_of(i)];                                                                  \
+      else                                                                                         \
+        enc_ = fmaf(-rho0, SIG_AT(cy_, cz_, xm_), s_x);                                            \
+      const float v_ = ds_ + enc_;                                                                 \
+      store_pop<ST>(pop + (i) * plane + rc.base[1 + cz_][1 + cy_] + xm_, kScaled ? v_ * scale : v_, \
+                    rng, sr);                                                                      \
+    }                                                                                              \
+  } while (0)
   // rest population: cu = cF = 0
-  store(0, fmaf(om1, d[0], fmaf(omega, fmaf(M0, m15usq, dM), m3uF)));
+  STORE_POP(0, fmaf(om1, d[0], fmaf(omega, fmaf(M0, m15usq, dM), m3uF)));
   // opposite pairs (i, i+1): cu and cF change sign, so
   //   omega d^eq + Omega = A +- B,  A = omega (dM + M0 (4.5 cu^2 - 1.5 u.u)) + cf (9 cu cF - 3 u.F),
   //                                 B = 3 omega M0 cu + 3 cf cF
@@ -392,9 +423,10 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
     const float t = fmaf(M0, fmaf(4.5f * cu, cu, m15usq), dM);
     const float A = fmaf(omega, t, fmaf(cf9 * cu, cF, m3uF));
     const float B = fmaf(oM03, cu, cf3 * cF);
-    store(i, fmaf(om1, d[i], A + B));
-    store(i + 1, fmaf(om1, d[i + 1], A - B));
+    STORE_POP(i, fmaf(om1, d[i], A + B));
+    STORE_POP(i + 1, fmaf(om1, d[i + 1], A - B));
   }
+#undef STORE_POP
 #undef EPS_AT
 #undef DEPS_AT
 #undef SIG_AT

@@ -69,10 +69,58 @@ def _time_steps(lat, steps, warmup):
     return a.elapsed_time(b) / steps
 
 
+def tune_step(lattice="D3Q19", storage="fp32", shape=(128, 128, 128), tau=0.6, steps=20, warmup=4,
+              cache: Cache | None = None, blocks=None, force=True):
+    """Time the row-staged kernel (when the lattice qualifies) and the
+    one-cell-per-thread kernel with each block shape on a lattice of this
+    size.  Caches and returns (best, timings): best = {"kernel": 1|2,
+    "block": [bx, by]}, timings in ms per step per candidate."""
+    import torch
+    cache = cache or Cache()
+    key = "step/" + bucket_key(lattice, storage, shape)
+    hit = cache.get(key)
+    if hit and not force:
+        return hit["best"], hit["ms"]
+    stream = torch.cuda.current_stream().cuda_stream
+    nx, ny, nz = (list(shape) + [1, 1])[:3]
+    timings, configs = {}, {}
+
+    def trial(name, kernel, block):
+        try:
+            lat = lbm.Lattice(lattice, (nx, ny, nz), tau=tau, storage=storage, stream=stream,
+                              block=block, kernel=kernel)
+        except lbm.LbmError:
+            return
+        lat.set_force((1e-6, 0, 0))
+        lat.init_equilibrium()
+        timings[name] = _time_steps(lat, steps, warmup)
+        configs[name] = {"kernel": kernel, "block": list(block)}
+        lat.close()
+    if storage != "fp64":
+        trial("row", 2, (0, 0))
+    for bx, by in blocks or BLOCK_CANDIDATES:
+        if by > ny or bx > 2 * max(nx, 32):
+            continue
+        trial(f"cell{bx}x{by}", 1, (bx, by))
+    best = min(timings, key=timings.get)
+    cache.put(key, {"best": configs[best], "ms": timings, "shape": [nx, ny, nz]})
+    return configs[best], timings
+
+
+def best_config(lattice, storage, shape, cache: Cache | None = None):
+    """Cached (kernel, block) for this size bucket, or the library default
+    (automatic kernel choice, default block)."""
+    cache = cache or Cache()
+    hit = cache.get("step/" + bucket_key(lattice, storage, shape))
+    if hit:
+        return hit["best"]["kernel"], tuple(hit["best"]["block"])
+    return 0, (0, 0)
+
+
 def tune_block(lattice="D3Q19", storage="fp32", shape=(128, 128, 128), tau=0.6, steps=20,
                warmup=4, cache: Cache | None = None, candidates=None, eps=None, force=True):
-    """Time each block shape on a lattice of this size; return the best
-    (bx, by) and the per-candidate milliseconds per step."""
+    """Time each block shape of the one-cell-per-thread kernel on a lattice
+    of this size; return the best (bx, by) and the per-candidate ms/step."""
     import torch
     cache = cache or Cache()
     key = "block/" + bucket_key(lattice, storage, shape)
@@ -86,7 +134,7 @@ def tune_block(lattice="D3Q19", storage="fp32", shape=(128, 128, 128), tau=0.6, 
         if by > ny or bx > 2 * max(nx, 32):
             continue
         lat = lbm.Lattice(lattice, (nx, ny, nz), tau=tau, storage=storage, stream=stream,
-                          block=(bx, by))
+                          block=(bx, by), kernel="cell")
         if eps is not None:
             lat.set_epsilon(eps)
         lat.set_force((1e-6, 0, 0))
