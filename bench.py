@@ -63,7 +63,7 @@ def peak_hbm():
 def profiled_traffic(storage: str, kernel_src_hash: str):
     """DRAM bytes per launch from the committed ncu summary, if the kernel
     source has not changed since it was captured."""
-    path = os.path.join(ROOT, "profiles", f"step_fast_d3q19_{storage}_256.md")
+    path = os.path.join(ROOT, "profiles", f"step_row_d3q19_{storage}.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
@@ -76,7 +76,7 @@ def profiled_traffic(storage: str, kernel_src_hash: str):
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for name in ("step_fast.cuh", "step_fast_d3q19.cu", "lattice.cuh", "internal.h"):
+    for name in ("step_row.cuh", "step_fast.cuh", "step_fast_d3q19.cu", "lattice.cuh", "internal.h"):
         with open(os.path.join(ROOT, "paper_2208_09267_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -281,7 +281,7 @@ def run_batched(count=64, steps=200, storages=("fp16", "fp32")):
     eps_of = {id(s): s.eps().ravel().astype(np.float32) for s in specs}
     for storage in storages:
         lats = [make(storage, s) for s in specs]
-        b = lbm.Batch(max_members=count, max_tiles=sum((lt.n + 4095) // 4096 for lt in lats) + 8,
+        b = lbm.Batch(max_members=count, max_tiles=sum((lt.stored + 4095) // 4096 for lt in lats) + 8,
                       stream=stream)
         for lt in lats:
             b.add(lt, steps + 20)

@@ -103,9 +103,9 @@ typedef struct {
                                step kernel; 0 = library default */
   int kernel;               /* step kernel: 0 = automatic, 1 = one cell per
                                thread, 2 = row-staged (whole x-rows staged in
-                               shared memory by TMA bulk copies; needs nx a
-                               multiple of 4 (FP32) or 8 (FP16), 32 <= nx <= 512,
-                               no walls on x; LBM_EINVAL otherwise) */
+                               shared memory by TMA bulk copies; needs
+                               8 <= nx <= 512, FP32 or FP16 storage and no
+                               walls on x; LBM_EINVAL otherwise) */
   int fp16_rounding;        /* LBM_FP16_SHIFTED stores: 0 = stochastic
                                rounding (unbiased; random bits from a
                                counter-based hash of cell and step, so runs
@@ -249,8 +249,9 @@ LBM_API int lbm_vanse_load_state(lbm_vanse_t h, const void *buf, size_t size);
 
 /* Create an empty batch on `stream` (cudaStream_t or NULL) holding at most
    max_members lattices and max_tiles tiles; tile_cells is the number of
-   cells one tile covers (0 = library default).  Members must use FP32 or
-   FP16 storage. */
+   stored cells one tile covers (0 = library default).  A member holds
+   ceil(nxp*ny*nz / tile_cells) tiles, nxp being nx rounded up to a multiple
+   of 8 (the stored row pitch).  Members must use FP32 or FP16 storage. */
 LBM_API int lbm_vanse_batch_create(int max_members, int max_tiles, int tile_cells, void *stream,
                            lbm_vanse_batch_t *out);
 LBM_API void lbm_vanse_batch_destroy(lbm_vanse_batch_t b);

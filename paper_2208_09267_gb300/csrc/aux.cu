@@ -16,17 +16,18 @@ cudaError_t launch_step_exact(int lattice, const LatticeDev *L_dev, bool odd, in
 cudaError_t launch_step_row_d2q9(const LatticeDev *, int, bool, int, int, const StepLaunch &, cudaStream_t);
 cudaError_t launch_step_row_d3q19(const LatticeDev *, int, bool, int, int, const StepLaunch &, cudaStream_t);
 cudaError_t launch_step_row_d3q27(const LatticeDev *, int, bool, int, int, const StepLaunch &, cudaStream_t);
-int plan_row_d2q9(int, int, int, int, unsigned, StepLaunch &);
-int plan_row_d3q19(int, int, int, int, unsigned, StepLaunch &);
-int plan_row_d3q27(int, int, int, int, unsigned, StepLaunch &);
+int plan_row_d2q9(int, int, int, int, int, unsigned, StepLaunch &);
+int plan_row_d3q19(int, int, int, int, int, unsigned, StepLaunch &);
+int plan_row_d3q27(int, int, int, int, int, unsigned, StepLaunch &);
 
-int plan_row_kernel(int lattice, int storage, int nx, int ny, int nz, unsigned walls, StepLaunch &ls) {
+int plan_row_kernel(int lattice, int storage, int nx, int nxp, int ny, int nz, unsigned walls,
+                    StepLaunch &ls) {
   ls.row = 0;
   if (storage == 0) return 0;
   switch (lattice) {
-    case 0: return plan_row_d2q9(storage, nx, ny, nz, walls, ls);
-    case 1: return plan_row_d3q19(storage, nx, ny, nz, walls, ls);
-    case 2: return plan_row_d3q27(storage, nx, ny, nz, walls, ls);
+    case 0: return plan_row_d2q9(storage, nx, nxp, ny, nz, walls, ls);
+    case 1: return plan_row_d3q19(storage, nx, nxp, ny, nz, walls, ls);
+    case 2: return plan_row_d3q27(storage, nx, nxp, ny, nz, walls, ls);
   }
   return 0;
 }
@@ -109,34 +110,64 @@ cudaError_t launch_finalize(const double *partials, int nblocks, double *out, cu
   return cudaGetLastError();
 }
 
-__global__ void shift_kernel(const float *eps, __half *sig, int nx, int ny, int nz, unsigned qa, float w0,
-                             float w1) {
-  const long long N = (long long)nx * ny * nz;
+__global__ void shift_kernel(const float *eps, __half *sig, int nx, int nxp, int ny, int nz, unsigned qa,
+                             float w0, float w1) {
+  const long long N = (long long)nxp * ny * nz;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
        c += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(c % nx);
-    const long long r = c / nx;
+    const int x = (int)(c % nxp);
+    if (x >= nx) {  // row padding: a valid value that nothing decodes
+      sig[c] = __float2half_rn(1.0f);
+      continue;
+    }
+    const long long r = c / nxp;
     const int y = (int)(r % ny), z = (int)(r / ny);
     float nb = 0.f;
     if (qa & 1u) nb += eps[c - x + (x == nx - 1 ? 0 : x + 1)] + eps[c - x + (x == 0 ? nx - 1 : x - 1)];
     if (qa & 2u) {
       const long long row = (long long)z * ny;
-      nb += eps[(row + (y == ny - 1 ? 0 : y + 1)) * nx + x] + eps[(row + (y == 0 ? ny - 1 : y - 1)) * nx + x];
+      nb += eps[(row + (y == ny - 1 ? 0 : y + 1)) * nxp + x] + eps[(row + (y == 0 ? ny - 1 : y - 1)) * nxp + x];
     }
     if (qa & 4u) {
-      const long long pl = (long long)ny * nx;
-      nb += eps[(long long)(z == nz - 1 ? 0 : z + 1) * pl + (long long)y * nx + x] +
-            eps[(long long)(z == 0 ? nz - 1 : z - 1) * pl + (long long)y * nx + x];
+      const long long pl = (long long)ny * nxp;
+      nb += eps[(long long)(z == nz - 1 ? 0 : z + 1) * pl + (long long)y * nxp + x] +
+            eps[(long long)(z == 0 ? nz - 1 : z - 1) * pl + (long long)y * nxp + x];
     }
     sig[c] = __float2half_rn(fmaf(w0, eps[c], w1 * nb));
   }
 }
 
 cudaError_t launch_shift(const LatticeDev &h, const float *eps, __half *sig, cudaStream_t s) {
-  const long long N = (long long)h.nx * h.ny * h.nz;
+  const long long N = (long long)h.nxp * h.ny * h.nz;
   long long g = (N + 255) / 256;
   if (g > 152LL * 32) g = 152LL * 32;
-  shift_kernel<<<(int)g, 256, 0, s>>>(eps, sig, h.nx, h.ny, h.nz, h.quad_axes, (float)h.qw0, (float)h.qw1);
+  shift_kernel<<<(int)g, 256, 0, s>>>(eps, sig, h.nx, h.nxp, h.ny, h.nz, h.quad_axes, (float)h.qw0,
+                                      (float)h.qw1);
+  return cudaGetLastError();
+}
+
+__global__ void pitch_convert_kernel(const void *in, int in_f64, void *out, int out_f64, int nx, int nxp,
+                                     long long rows) {
+  const long long n = (long long)nx * rows;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / nx, x = i % nx;
+    const double v = in_f64 ? static_cast<const double *>(in)[i] : (double)static_cast<const float *>(in)[i];
+    const long long o = r * nxp + x;
+    if (out_f64)
+      static_cast<double *>(out)[o] = v;
+    else
+      static_cast<float *>(out)[o] = (float)v;
+  }
+}
+
+cudaError_t launch_pitch_convert(const void *in, int in_f64, void *out, int out_f64, int nx, int nxp,
+                                 long long rows, cudaStream_t s) {
+  const long long n = (long long)nx * rows;
+  if (n <= 0) return cudaSuccess;
+  long long g = (n + 255) / 256;
+  if (g > 152LL * 32) g = 152LL * 32;
+  pitch_convert_kernel<<<(int)g, 256, 0, s>>>(in, in_f64, out, out_f64, nx, nxp, rows);
   return cudaGetLastError();
 }
 

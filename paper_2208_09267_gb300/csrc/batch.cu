@@ -60,14 +60,15 @@ __global__ void __launch_bounds__(kBatchBlock) batch_step_kernel(const BatchMemb
     const long long n = L.n + k;
     const long long last = (budget < kmax ? budget : kmax) - 1;
     const bool red_here = RED && k == last;
-    const int nx = L.nx, ny = L.ny;
-    const int c_end = tile.y0 + tile.ny;  // y0 = first cell, ny = cell count (linear tile)
+    const int nx = L.nx, ny = L.ny, nxp = L.nxp;
+    const int c_end = tile.y0 + tile.ny;  // y0 = first stored cell, ny = cell count (linear tile)
     RedAcc acc;
 #pragma unroll
     for (int j = 0; j < kRedWidth; ++j) acc.v[j] = 0.0;
     for (int c = tile.y0 + threadIdx.x; c < c_end; c += blockDim.x) {
-      const int x = c % nx;
-      const int r = c / nx;
+      const int x = c % nxp;
+      if (x >= nx) continue;  // row padding
+      const int r = c / nxp;
       const int y = r % ny;
       const int z = r / ny;
       if (red_here) {

@@ -16,12 +16,16 @@
 namespace lbm {
 
 struct LatticeDev {
-  // geometry: cells (z*ny + y)*nx + x; population slot i of a cell lives at
-  // pop[i*plane + cell]
+  // geometry: cell (x, y, z) is stored at index (z*ny + y)*nxp + x, rows
+  // padded to a pitch of nxp >= nx elements (16-byte aligned rows for the
+  // bulk copies); population slot i of a cell lives at pop[i*plane + cell].
+  // Caller-facing fields are dense (x fastest, pitch nx).
   int nx, ny, nz;
   int lattice;             // 0 D2Q9, 1 D3Q19, 2 D3Q27
-  long long ncell;
+  long long ncell;         // nxp * ny * nz: stored cells, padding included
   long long plane;         // elements between population planes (>= ncell)
+  int nxp;                 // row pitch
+  int pad0;
   unsigned walls;          // axis bits of solid first/last layers
   unsigned quad_axes;      // axis bits entering eq. (quad)
   int storage;             // 0 FP64, 1 FP32, 2 FP16
@@ -69,7 +73,7 @@ struct StepLaunch {
 // Plan the row-staged kernel for a lattice: fills ls.row* and returns 1 when
 // the lattice qualifies (storage FP32/FP16, rows 16-byte aligned, nx <= 512,
 // no x walls, shared memory fits), else 0.
-int plan_row_kernel(int lattice, int storage, int nx, int ny, int nz, unsigned walls, StepLaunch &ls);
+int plan_row_kernel(int lattice, int storage, int nx, int nxp, int ny, int nz, unsigned walls, StepLaunch &ls);
 
 // Default/chosen block shape -> launch geometry for a lattice.
 StepLaunch make_launch(int nx, int ny, int nz, int bx, int by);
@@ -115,6 +119,11 @@ cudaError_t launch_validate(const void *data, long long n, int is_f64, int unit,
 // Float -> double / double -> float conversions for field uploads.
 cudaError_t launch_convert_f2d(const float *in, double *out, long long n, cudaStream_t s);
 cudaError_t launch_convert_d2f(const double *in, float *out, long long n, cudaStream_t s);
+
+// Dense (row length nx) device array of `rows` rows -> pitched array (row
+// pitch nxp), converting float <-> double as needed.
+cudaError_t launch_pitch_convert(const void *in, int in_f64, void *out, int out_f64, int nx, int nxp,
+                                 long long rows, cudaStream_t s);
 
 // ---- batched stepping ---------------------------------------------------
 

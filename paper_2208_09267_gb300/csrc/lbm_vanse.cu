@@ -35,7 +35,9 @@ struct lbm_vanse {
   LatticeDev *d = nullptr;  // device descriptor
   cudaStream_t stream = nullptr;
   int Q = 0, D = 0;
-  long long N = 0;
+  long long N = 0;        // cells, nx*ny*nz (the caller's dense layout)
+  long long Ni = 0;       // stored cells, nxp*ny*nz (rows padded to the pitch)
+  int nxp = 0;
   void *pop = nullptr;
   void *eps_buf[2] = {nullptr, nullptr};
   __half *sig_buf[2] = {nullptr, nullptr};  // shift sigma of each phi_ref buffer
@@ -139,10 +141,15 @@ static int validate_params(const lbm_vanse_params *p, std::string &why) {
 
 static long long plane_of(long long N) { return (N + 63) / 64 * 64; }
 
+// Stored row pitch: nx rounded up to 8 elements, so that every row of every
+// field starts on a 16-byte boundary and is a whole number of 16-byte units
+// (the bulk-copy rule), for 2-, 4- and 8-byte elements alike.
+static int pitch_of(int nx) { return (nx + 7) / 8 * 8; }
+
 extern "C" size_t lbm_vanse_device_bytes(const lbm_vanse_params *p, int with_deps, int with_force_field) {
   std::string why;
   if (!validate_params(p, why)) return 0;
-  const long long N = (long long)p->nx * p->ny * p->nz;
+  const long long N = (long long)pitch_of(p->nx) * p->ny * p->nz;  // stored cells
   const int Q = kQ[p->lattice];
   const size_t fe = p->storage == LBM_FP64 ? 8 : 4;
   size_t b = (size_t)Q * plane_of(N) * kElem[p->storage];  // populations
@@ -219,6 +226,8 @@ extern "C" int lbm_vanse_create(const lbm_vanse_params *p, lbm_vanse_t *out) {
   h->Q = kQ[p->lattice];
   h->D = kD[p->lattice];
   h->N = (long long)p->nx * p->ny * p->nz;
+  h->nxp = pitch_of(p->nx);
+  h->Ni = (long long)h->nxp * p->ny * p->nz;
   h->field_elem = p->storage == LBM_FP64 ? 8 : 4;
   const unsigned axes_mask = p->lattice == LBM_D2Q9 ? 3u : 7u;
   const unsigned qa = p->quad_axes ? p->quad_axes : axes_mask;
@@ -232,8 +241,9 @@ extern "C" int lbm_vanse_create(const lbm_vanse_params *p, lbm_vanse_t *out) {
   m.ny = p->ny;
   m.nz = p->nz;
   m.lattice = p->lattice;
-  m.ncell = h->N;
-  m.plane = plane_of(h->N);
+  m.ncell = h->Ni;
+  m.plane = plane_of(h->Ni);
+  m.nxp = h->nxp;
   m.walls = p->walls;
   m.quad_axes = qa;
   m.storage = p->storage;
@@ -254,7 +264,7 @@ extern "C" int lbm_vanse_create(const lbm_vanse_params *p, lbm_vanse_t *out) {
   h->ls = lbm::make_launch(p->nx, p->ny, p->nz, p->block_x, p->block_y);
   h->nblocks = (int)(h->ls.grid.x * h->ls.grid.y * h->ls.grid.z);
   if (p->kernel != 1 && p->storage != LBM_FP64) {
-    const int ok = lbm::plan_row_kernel(p->lattice, p->storage, p->nx, p->ny, p->nz, p->walls, h->ls);
+    const int ok = lbm::plan_row_kernel(p->lattice, p->storage, p->nx, h->nxp, p->ny, p->nz, p->walls, h->ls);
     if (!ok && p->kernel == 2) {
       delete h;
       return fail(nullptr, LBM_EINVAL, "the row-staged kernel does not fit this lattice");
@@ -267,14 +277,14 @@ extern "C" int lbm_vanse_create(const lbm_vanse_params *p, lbm_vanse_t *out) {
   int rc;
   const size_t pop_bytes = (size_t)h->Q * m.plane * kElem[p->storage];
   if ((rc = dev_alloc(h, &h->pop, pop_bytes)) ||
-      (rc = dev_alloc(h, &h->eps_buf[0], (size_t)h->N * h->field_elem)) ||
-      (rc = dev_alloc(h, &h->eps_buf[1], (size_t)h->N * h->field_elem)) ||
+      (rc = dev_alloc(h, &h->eps_buf[0], (size_t)h->Ni * h->field_elem)) ||
+      (rc = dev_alloc(h, &h->eps_buf[1], (size_t)h->Ni * h->field_elem)) ||
       (rc = dev_alloc(h, (void **)&h->partials, (size_t)nblocks_alloc * lbm::kRedWidth * sizeof(double))) ||
       (rc = dev_alloc(h, (void **)&h->stats_dev, 64 * sizeof(double))) ||
       (rc = dev_alloc(h, (void **)&h->status, 64)) ||
       (rc = dev_alloc(h, (void **)&h->d, sizeof(LatticeDev))) ||
-      (p->storage != LBM_FP64 && ((rc = dev_alloc(h, (void **)&h->sig_buf[0], (size_t)h->N * 2)) ||
-                                  (rc = dev_alloc(h, (void **)&h->sig_buf[1], (size_t)h->N * 2))))) {
+      (p->storage != LBM_FP64 && ((rc = dev_alloc(h, (void **)&h->sig_buf[0], (size_t)h->Ni * 2)) ||
+                                  (rc = dev_alloc(h, (void **)&h->sig_buf[1], (size_t)h->Ni * 2))))) {
     g_last_error = h->err;
     lbm_vanse_destroy(h);
     return rc;
@@ -290,14 +300,20 @@ extern "C" int lbm_vanse_create(const lbm_vanse_params *p, lbm_vanse_t *out) {
   std::vector<float> ones_f;
   const void *src;
   if (h->field_elem == 8) {
-    ones_d.assign(h->N, 1.0);
+    ones_d.assign(h->Ni, 1.0);
     src = ones_d.data();
   } else {
-    ones_f.assign(h->N, 1.0f);
+    ones_f.assign(h->Ni, 1.0f);
     src = ones_f.data();
   }
-  cudaError_t e = cudaMemcpyAsync(h->eps_buf[0], src, (size_t)h->N * h->field_elem,
+  // both phi buffers start as 1 everywhere, row padding included (padding
+  // keeps a valid value that no kernel uses)
+  cudaError_t e = cudaMemcpyAsync(h->eps_buf[0], src, (size_t)h->Ni * h->field_elem,
                                   cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->eps_buf[1], src, (size_t)h->Ni * h->field_elem, cudaMemcpyHostToDevice,
+                        h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->pop, 0, pop_bytes, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, 64, h->stream);
   if (e != cudaSuccess) {
@@ -334,39 +350,41 @@ extern "C" int lbm_vanse_create(const lbm_vanse_params *p, lbm_vanse_t *out) {
   return LBM_OK;
 }
 
-// Copy n values of a field to a device buffer of the handle's field type.
-// src_is_f64 tells the caller's element type.
-static int upload_field(lbm_vanse_t h, void *dst, const void *src, long long n, int src_is_f64,
+// Copy `ncomp` dense fields (nx*ny*nz values each, x fastest) of the
+// caller's element type into a pitched device buffer of the handle's field
+// type (component a at a*Ni, rows at pitch nxp).  Host sources are copied
+// before the call returns.
+static int upload_field(lbm_vanse_t h, void *dst, const void *src, int ncomp, int src_is_f64,
                         int on_device) {
   const bool dst_f64 = h->field_elem == 8;
-  if (on_device) {
-    if ((bool)src_is_f64 == dst_f64) {
-      CUDA_TRY(h, cudaMemcpyAsync(dst, src, (size_t)n * h->field_elem, cudaMemcpyDeviceToDevice, h->stream));
-    } else if (src_is_f64) {
-      CUDA_TRY(h, lbm::launch_convert_d2f(static_cast<const double *>(src), static_cast<float *>(dst), n, h->stream));
-    } else {
-      CUDA_TRY(h, lbm::launch_convert_f2d(static_cast<const float *>(src), static_cast<double *>(dst), n, h->stream));
-    }
-    return LBM_OK;
-  }
+  const int nx = h->p.nx, nxp = h->nxp;
+  const long long rows = (long long)h->p.ny * h->p.nz * ncomp;
+  const size_t fe = h->field_elem;
   if ((bool)src_is_f64 == dst_f64) {
-    // a pinned source would be read after the return: wait for the copy so
-    // that the caller may reuse the buffer at once
-    CUDA_TRY(h, cudaMemcpyAsync(dst, src, (size_t)n * h->field_elem, cudaMemcpyHostToDevice, h->stream));
-    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    CUDA_TRY(h, cudaMemcpy2DAsync(dst, (size_t)nxp * fe, src, (size_t)nx * fe, (size_t)nx * fe, (size_t)rows,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+    // a pinned host source would be read after the return: wait for the copy
+    if (!on_device) CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return LBM_OK;
   }
+  if (on_device) {
+    CUDA_TRY(h, lbm::launch_pitch_convert(src, src_is_f64, dst, dst_f64, nx, nxp, rows, h->stream));
+    return LBM_OK;
+  }
+  const long long n = (long long)nx * rows;
   if (dst_f64) {
     std::vector<double> tmp(n);
-    const float *s = static_cast<const float *>(src);
-    for (long long i = 0; i < n; ++i) tmp[i] = (double)s[i];
-    CUDA_TRY(h, cudaMemcpyAsync(dst, tmp.data(), (size_t)n * 8, cudaMemcpyHostToDevice, h->stream));
+    const float *sp = static_cast<const float *>(src);
+    for (long long i = 0; i < n; ++i) tmp[i] = (double)sp[i];
+    CUDA_TRY(h, cudaMemcpy2DAsync(dst, (size_t)nxp * 8, tmp.data(), (size_t)nx * 8, (size_t)nx * 8, (size_t)rows,
+                                  cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   } else {
     std::vector<float> tmp(n);
-    const double *s = static_cast<const double *>(src);
-    for (long long i = 0; i < n; ++i) tmp[i] = (float)s[i];
-    CUDA_TRY(h, cudaMemcpyAsync(dst, tmp.data(), (size_t)n * 4, cudaMemcpyHostToDevice, h->stream));
+    const double *sp = static_cast<const double *>(src);
+    for (long long i = 0; i < n; ++i) tmp[i] = (float)sp[i];
+    CUDA_TRY(h, cudaMemcpy2DAsync(dst, (size_t)nxp * 4, tmp.data(), (size_t)nx * 4, (size_t)nx * 4, (size_t)rows,
+                                  cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   }
   return LBM_OK;
@@ -394,9 +412,12 @@ static int check_uploaded(lbm_vanse_t h, const void *dev, long long n, int is_f6
   CUDA_TRY(h, lbm::launch_validate(dev, n, is_f64, unit_interval ? 1 : 0, flag, h->stream));
   CUDA_TRY(h, cudaMemcpyAsync(host, flag, sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-  if (*host < n)
-    return fail(h, LBM_EINVAL, "%s[%lld] is %s", what, *host,
+  if (*host < n) {
+    // report the caller's dense index of the stored cell
+    const long long i = *host, row = i / h->nxp, x = i % h->nxp;
+    return fail(h, LBM_EINVAL, "%s[%lld] is %s", what, row * h->p.nx + x,
                 unit_interval ? "not finite or outside (0, 1]" : "not finite");
+  }
   return LBM_OK;
 }
 
@@ -409,12 +430,15 @@ static int set_epsilon_any(lbm_vanse_t h, const void *eps, const void *deps, lon
   const int dev_f64 = h->field_elem == 8;
   // host values are checked on the device after the upload; nothing of the
   // handle's state changes before both fields passed
-  if ((rc = upload_field(h, h->eps_buf[next], eps, h->N, is_f64, on_device))) return rc;
-  if (!on_device && (rc = check_uploaded(h, h->eps_buf[next], h->N, dev_f64, true, "eps_ref"))) return rc;
+  if ((rc = upload_field(h, h->eps_buf[next], eps, 1, is_f64, on_device))) return rc;
+  if (!on_device && (rc = check_uploaded(h, h->eps_buf[next], h->Ni, dev_f64, true, "eps_ref"))) return rc;
   if (deps) {
-    if (!h->deps && (rc = dev_alloc(h, &h->deps, (size_t)h->N * h->field_elem))) return rc;
-    if ((rc = upload_field(h, h->deps, deps, h->N, is_f64, on_device))) return rc;
-    if (!on_device && (rc = check_uploaded(h, h->deps, h->N, dev_f64, false, "deps_dt"))) return rc;
+    if (!h->deps) {
+      if ((rc = dev_alloc(h, &h->deps, (size_t)h->Ni * h->field_elem))) return rc;
+      CUDA_TRY(h, cudaMemsetAsync(h->deps, 0, (size_t)h->Ni * h->field_elem, h->stream));
+    }
+    if ((rc = upload_field(h, h->deps, deps, 1, is_f64, on_device))) return rc;
+    if (!on_device && (rc = check_uploaded(h, h->deps, h->Ni, dev_f64, false, "deps_dt"))) return rc;
     h->h.has_deps = 1;
   } else {
     h->h.has_deps = 0;
@@ -462,11 +486,18 @@ static int set_force_any(lbm_vanse_t h, const double *g, const void *field, cons
     }
   }
   if (field) {
-    if (!h->force && (rc = dev_alloc(h, &h->force, (size_t)n3 * h->field_elem))) return rc;
-    if ((rc = upload_field(h, h->force, field, n3, is_f64, on_device))) return rc;
+    const size_t fbytes = (size_t)3 * h->Ni * h->field_elem;
+    if (!h->force) {
+      if ((rc = dev_alloc(h, &h->force, fbytes))) return rc;
+      CUDA_TRY(h, cudaMemsetAsync(h->force, 0, fbytes, h->stream));
+    }
+    if ((rc = upload_field(h, h->force, field, 3, is_f64, on_device))) return rc;
     if (dfield) {
-      if (!h->dforce && (rc = dev_alloc(h, &h->dforce, (size_t)n3 * h->field_elem))) return rc;
-      if ((rc = upload_field(h, h->dforce, dfield, n3, is_f64, on_device))) return rc;
+      if (!h->dforce) {
+        if ((rc = dev_alloc(h, &h->dforce, fbytes))) return rc;
+        CUDA_TRY(h, cudaMemsetAsync(h->dforce, 0, fbytes, h->stream));
+      }
+      if ((rc = upload_field(h, h->dforce, dfield, 3, is_f64, on_device))) return rc;
     }
   }
   for (int a = 0; a < 3; ++a) h->h.g[a] = gv[a];
@@ -660,7 +691,7 @@ extern "C" int lbm_vanse_step(lbm_vanse_t h, long long max_steps, double residua
     return LBM_OK;
   }
   if (residual_tol > 0.0 && !h->u_prev) {
-    if ((rc = dev_alloc(h, (void **)&h->u_prev, (size_t)3 * h->N * sizeof(float)))) return rc;
+    if ((rc = dev_alloc(h, (void **)&h->u_prev, (size_t)3 * h->Ni * sizeof(float)))) return rc;
     h->h.have_prev = 0;
     h->last_check_n = -1;
   }
@@ -805,8 +836,8 @@ struct StateHeader {
 extern "C" int lbm_vanse_save_state(lbm_vanse_t h, void *buf, size_t *size) {
   if (!h || !size) return fail(h, LBM_EINVAL, "NULL argument");
   const size_t pop_bytes = (size_t)h->Q * h->h.plane * kElem[h->p.storage];
-  const size_t fb = (size_t)h->N * h->field_elem;
-  const size_t sb = h->p.storage == LBM_FP64 ? 0 : (size_t)h->N * 2;
+  const size_t fb = (size_t)h->Ni * h->field_elem;
+  const size_t sb = h->p.storage == LBM_FP64 ? 0 : (size_t)h->Ni * 2;
   const size_t total = sizeof(StateHeader) + pop_bytes + sb + 2 * fb + 6 * fb;
   if (!buf) {
     *size = total;
@@ -857,10 +888,10 @@ extern "C" int lbm_vanse_load_state(lbm_vanse_t h, const void *buf, size_t size)
   StateHeader hd;
   memcpy(&hd, buf, sizeof(hd));
   const size_t pop_bytes = (size_t)h->Q * h->h.plane * kElem[h->p.storage];
-  const size_t fb = (size_t)h->N * h->field_elem;
+  const size_t fb = (size_t)h->Ni * h->field_elem;
   if (memcmp(hd.magic, "LBMVANSE", 8) != 0 || hd.lattice != h->p.lattice || hd.storage != h->p.storage ||
       hd.nx != h->p.nx || hd.ny != h->p.ny || hd.nz != h->p.nz || hd.pop_bytes != pop_bytes ||
-      hd.field_bytes != fb || size < sizeof(StateHeader) + pop_bytes + (h->p.storage == LBM_FP64 ? 0 : (size_t)h->N * 2) + 8 * fb)
+      hd.field_bytes != fb || size < sizeof(StateHeader) + pop_bytes + (h->p.storage == LBM_FP64 ? 0 : (size_t)h->Ni * 2) + 8 * fb)
     return fail(h, LBM_EINVAL, "state does not match this lattice");
   int rc;
   const char *o = static_cast<const char *>(buf) + sizeof(hd);
@@ -869,7 +900,7 @@ extern "C" int lbm_vanse_load_state(lbm_vanse_t h, const void *buf, size_t size)
   // the current phi (and its shift) go to buffer 0; the shift the data is
   // encoded with goes to shift buffer 1 when a shift change is pending
   const int cur = 0, other = 1;
-  const size_t sb = h->p.storage == LBM_FP64 ? 0 : (size_t)h->N * 2;
+  const size_t sb = h->p.storage == LBM_FP64 ? 0 : (size_t)h->Ni * 2;
   CUDA_TRY(h, cudaMemcpyAsync(h->eps_buf[cur], o, fb, cudaMemcpyHostToDevice, h->stream));
   o += fb;
   if (sb) CUDA_TRY(h, cudaMemcpyAsync(h->sig_buf[other], o, sb, cudaMemcpyHostToDevice, h->stream));

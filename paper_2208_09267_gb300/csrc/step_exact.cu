@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(256) step_exact_kernel(const LatticeDev *__res
   const bool fluid = inside && !(L.walls && solid_at(L.walls, x, y, z, 0, 0, 0, L.nx, L.ny, L.nz));
   if (fluid) {
     const long long n = L.n + k;
-    const Coords C = make_coords(x, y, z, L.nx, L.ny, L.nz);
+    const Coords C = make_coords(x, y, z, L.nx, L.ny, L.nz, L.nxp);
     double *pop = static_cast<double *>(L.pop);
     double f[Q];
 #pragma unroll
@@ -265,8 +265,10 @@ __global__ void moments_kernel(const LatticeDev *__restrict__ Lp, double *rho, d
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
   if (x >= L.nx || y >= L.ny) return;
-  const Coords C = make_coords(x, y, z, L.nx, L.ny, L.nz);
-  const long long k = C.at(0, 0, 0), N = L.ncell;
+  const Coords C = make_coords(x, y, z, L.nx, L.ny, L.nz, L.nxp);
+  // outputs are dense: index (z*ny + y)*nx + x, N = nx*ny*nz
+  const long long k = ((long long)z * L.ny + y) * L.nx + x;
+  const long long N = (long long)L.nx * L.ny * L.nz;
   const bool odd = (L.n & 1) != 0;
   if (L.walls && solid_at(L.walls, x, y, z, 0, 0, 0, L.nx, L.ny, L.nz)) {
     if (rho) rho[k] = 0.0;
@@ -305,15 +307,18 @@ __global__ void init_kernel(const LatticeDev *__restrict__ Lp, const double *p0,
   const int z = blockIdx.z;
   if (x >= L.nx || y >= L.ny) return;
   if (L.walls && solid_at(L.walls, x, y, z, 0, 0, 0, L.nx, L.ny, L.nz)) return;
-  const Coords C = make_coords(x, y, z, L.nx, L.ny, L.nz);
-  const long long k = C.at(0, 0, 0), N = L.ncell;
+  const Coords C = make_coords(x, y, z, L.nx, L.ny, L.nz, L.nxp);
+  const long long k = C.at(0, 0, 0);
+  // p0, u0 are dense arrays: index (z*ny + y)*nx + x, N = nx*ny*nz
+  const long long kd = ((long long)z * L.ny + y) * L.nx + x;
+  const long long N = (long long)L.nx * L.ny * L.nz;
   const long long n = L.n;
   const bool odd = (n & 1) != 0;
   double u[3] = {0.0, 0.0, 0.0};
   if (u0)
-    for (int a = 0; a < D; ++a) u[a] = u0[a * N + k];
+    for (int a = 0; a < D; ++a) u[a] = u0[a * N + kd];
   double usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-  const double rt = L.rho0 + (p0 ? 3.0 * p0[k] : 0.0);
+  const double rt = L.rho0 + (p0 ? 3.0 * p0[kd] : 0.0);
   const double dn = (double)(n - L.n_eps);
   double mass;
   if (mode & 1) {
@@ -354,13 +359,13 @@ __global__ void getpop_kernel(const LatticeDev *__restrict__ Lp, double *out) {
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
   if (x >= L.nx || y >= L.ny) return;
-  const Coords C = make_coords(x, y, z, L.nx, L.ny, L.nz);
-  const long long k = C.at(0, 0, 0);
+  const Coords C = make_coords(x, y, z, L.nx, L.ny, L.nz, L.nxp);
+  const long long kd = ((long long)z * L.ny + y) * L.nx + x;  // dense output index
   const bool solid = L.walls && solid_at(L.walls, x, y, z, 0, 0, 0, L.nx, L.ny, L.nz);
   const bool odd = (L.n & 1) != 0;
 #pragma unroll
   for (int i = 0; i < Q; ++i)
-    out[k * Q + i] = solid ? 0.0 : load_f<LAT>(L, slot_of<LAT>(L, C, odd, i, x, y, z), i);
+    out[kd * Q + i] = solid ? 0.0 : load_f<LAT>(L, slot_of<LAT>(L, C, odd, i, x, y, z), i);
 }
 
 // ---- dispatch ----------------------------------------------------------------

@@ -98,15 +98,15 @@ __device__ __forceinline__ void store_pop<__half>(__half *p, float v, SRng &rng,
 
 struct Coords {
   int xs[3], ys[3], zs[3];  // coordinate of offset -1, 0, +1 (periodic)
-  int nx, ny;
+  int nxp, ny;              // row pitch, rows per plane
   __device__ __forceinline__ long long at(int cx, int cy, int cz) const {
-    return ((long long)zs[cz + 1] * ny + ys[cy + 1]) * nx + xs[cx + 1];
+    return ((long long)zs[cz + 1] * ny + ys[cy + 1]) * nxp + xs[cx + 1];
   }
 };
 
-__device__ __forceinline__ Coords make_coords(int x, int y, int z, int nx, int ny, int nz) {
+__device__ __forceinline__ Coords make_coords(int x, int y, int z, int nx, int ny, int nz, int nxp) {
   Coords c;
-  c.nx = nx;
+  c.nxp = nxp;
   c.ny = ny;
   c.xs[0] = x == 0 ? nx - 1 : x - 1;
   c.xs[1] = x;
@@ -142,7 +142,7 @@ __device__ __forceinline__ void update_cell_fast(const LatticeDev &L, long long 
   const unsigned walls = L.walls;
   if (walls && solid_at(walls, x, y, z, 0, 0, 0, nx, ny, nz)) return;
 
-  const Coords C = make_coords(x, y, z, nx, ny, nz);
+  const Coords C = make_coords(x, y, z, nx, ny, nz, L.nxp);
   const long long cell = C.at(0, 0, 0);
   const long long plane = L.plane;
   ST *__restrict__ pop = static_cast<ST *>(L.pop);

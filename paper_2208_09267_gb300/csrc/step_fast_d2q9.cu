@@ -44,9 +44,9 @@ cudaError_t launch_step_row_d2q9(const LatticeDev *L_dev, int storage, bool odd,
   return cudaErrorInvalidValue;
 }
 
-int plan_row_d2q9(int storage, int nx, int ny, int nz, unsigned walls, StepLaunch &ls) {
-  if (storage == 1) return plan_row_t<D2Q9, float, LBM_ROW_MINB_D2Q9>(nx, ny, nz, walls, ls);
-  if (storage == 2) return plan_row_t<D2Q9, __half, LBM_ROW_MINB_D2Q9>(nx, ny, nz, walls, ls);
+int plan_row_d2q9(int storage, int nx, int nxp, int ny, int nz, unsigned walls, StepLaunch &ls) {
+  if (storage == 1) return plan_row_t<D2Q9, float, LBM_ROW_MINB_D2Q9>(nx, nxp, ny, nz, walls, ls);
+  if (storage == 2) return plan_row_t<D2Q9, __half, LBM_ROW_MINB_D2Q9>(nx, nxp, ny, nz, walls, ls);
   return 0;
 }
 

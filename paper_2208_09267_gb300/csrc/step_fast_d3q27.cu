@@ -44,9 +44,9 @@ cudaError_t launch_step_row_d3q27(const LatticeDev *L_dev, int storage, bool odd
   return cudaErrorInvalidValue;
 }
 
-int plan_row_d3q27(int storage, int nx, int ny, int nz, unsigned walls, StepLaunch &ls) {
-  if (storage == 1) return plan_row_t<D3Q27, float, LBM_ROW_MINB_D3Q27>(nx, ny, nz, walls, ls);
-  if (storage == 2) return plan_row_t<D3Q27, __half, LBM_ROW_MINB_D3Q27>(nx, ny, nz, walls, ls);
+int plan_row_d3q27(int storage, int nx, int nxp, int ny, int nz, unsigned walls, StepLaunch &ls) {
+  if (storage == 1) return plan_row_t<D3Q27, float, LBM_ROW_MINB_D3Q27>(nx, nxp, ny, nz, walls, ls);
+  if (storage == 2) return plan_row_t<D3Q27, __half, LBM_ROW_MINB_D3Q27>(nx, nxp, ny, nz, walls, ls);
   return 0;
 }
 

@@ -130,7 +130,7 @@ __device__ __forceinline__ RowCtx make_row_ctx(const LatticeDev &L, int y, int z
   for (int dz = -1; dz <= 1; ++dz)
     for (int dy = -1; dy <= 1; ++dy) {
       const int yy = wrapi(y + dy, L.ny), zz = wrapi(z + dz, L.nz);
-      c.base[dz + 1][dy + 1] = (zz * L.ny + yy) * L.nx;
+      c.base[dz + 1][dy + 1] = (zz * L.ny + yy) * L.nxp;
       const bool sol = ((L.walls & 2u) && (y + dy <= 0 || y + dy >= L.ny - 1)) ||
                        ((L.walls & 4u) && (z + dz <= 0 || z + dz >= L.nz - 1));
       if (sol) c.solid |= 1u << ((dz + 1) * 3 + (dy + 1));
@@ -171,9 +171,10 @@ __device__ __forceinline__ void issue_row(const LatticeDev &L, unsigned char *st
   using Lay = RowLayout<LAT, ST, ODD, PITCH>;
   const int lane = threadIdx.x & 31;
   const bool tv = L.has_deps != 0;
-  const int nx = L.nx;
-  const unsigned pbytes = (unsigned)nx * (unsigned)sizeof(ST), sbytes = (unsigned)nx * 2u,
-                 rbytes = (unsigned)nx * 4u;
+  // whole stored rows (pitch nxp, a multiple of 8 elements: 16-byte sizes)
+  const int nxp = L.nxp;
+  const unsigned pbytes = (unsigned)nxp * (unsigned)sizeof(ST), sbytes = (unsigned)nxp * 2u,
+                 rbytes = (unsigned)nxp * 4u;
   const int nfield = Lay::kEpsRows + (tv ? Lay::kDepsRows : 0);
   const int ncopies = LAT::Q + Lay::kSigRows + nfield;
   if (lane == 0)
@@ -253,6 +254,7 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
 #define OWN_SRC(i) (!ODD || (i) == 0 || (WALLS && ((rc.solid >> ((1 - LAT::c((i), 2)) * 3 + (1 - LAT::c((i), 1)))) & 1u)))
 #define OWN_DST(i) (!ODD || (i) == 0 || (WALLS && ((rc.solid >> ((1 + LAT::c((i), 2)) * 3 + (1 + LAT::c((i), 1)))) & 1u)))
 
+  if (x >= nx) return;  // lane past the end of a row that is not a multiple of 32
   const int xs[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};
   const int cell = rc.base[1][1] + x;
   const float e_own = EPS_AT(0, 0, x);
@@ -534,7 +536,7 @@ __global__ void __launch_bounds__(kRowBlock, MINB) step_row_kernel(const Lattice
       }
       // 32-cell chunks of the row, dealt round-robin to the consumer warps
       // across rows so that every warp gets the same share
-      const int nchunks = L.nx >> 5;
+      const int nchunks = (L.nx + 31) >> 5;
       const int first = (warp - (int)(((long long)j * nchunks) % kConsumerWarps) + kConsumerWarps) % kConsumerWarps;
       for (int c = first; c < nchunks; c += kConsumerWarps)
         update_row_chunk<LAT, ST, ODD, RED, WALLS, PITCH>(L, stages + s * Lay::kStageBytes, ctx[s], n,
@@ -618,10 +620,10 @@ int configure_row_v(int &occ) {
 }
 
 template <class LAT, class ST, int MINB>
-int plan_row_t(int nx, int ny, int nz, unsigned walls, StepLaunch &ls) {
-  if (nx % 32 != 0 || nx > 512 || nx < 32) return 0;
+int plan_row_t(int nx, int nxp, int ny, int nz, unsigned walls, StepLaunch &ls) {
+  if (nxp % 8 != 0 || nxp > 512 || nx < 8) return 0;
   if (walls & 1u) return 0;
-  const bool w = (walls & 6u) != 0, p512 = nx > 256;
+  const bool w = (walls & 6u) != 0, p512 = nxp > 256;
   int occ = 0, ok;
   if (p512)
     ok = w ? configure_row_v<LAT, ST, true, 512, (MINB > 1 ? MINB - 1 : 1)>(occ)

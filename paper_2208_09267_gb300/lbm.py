@@ -166,6 +166,12 @@ def current_stream_ptr():
     return torch.cuda.current_stream().cuda_stream
 
 
+def stored_cells(nx: int, ny: int, nz: int) -> int:
+    """Cells a lattice holds on the device: every x-row is stored at a pitch
+    of nx rounded up to 8 elements (the unit a batch tile counts)."""
+    return (nx + 7) // 8 * 8 * ny * nz
+
+
 class Lattice:
     """One lattice handle (lbm_vanse_t).  Shapes follow the C ABI: fields are
     flat arrays of N = nx*ny*nz values with x fastest; vector fields have
@@ -199,6 +205,8 @@ class Lattice:
         self.d = DIM_OF[p.lattice]
         self.nx, self.ny, self.nz = p.nx, p.ny, p.nz
         self.n = p.nx * p.ny * p.nz
+        # cells as stored on the device: x-rows padded to a multiple of 8
+        self.stored = stored_cells(p.nx, p.ny, p.nz)
         self.f64 = p.storage == 0
 
     # -- lifetime ---------------------------------------------------------

@@ -58,7 +58,7 @@ class Request:
 def request_bytes(spec: LatticeSpec, storage: str) -> int:
     nz, ny, nx = spec.shape
     base = lbm.device_bytes(spec.lattice, (nx, ny, nz), storage)
-    return base + 3 * spec.cells * 4  # the residual buffer of a batch member
+    return base + 3 * lbm.stored_cells(nx, ny, nz) * 4  # the residual buffer of a batch member
 
 
 @dataclass

@@ -176,7 +176,7 @@ def tune_tiles(specs, storage="fp16", steps=10, candidates=None, cache: Cache | 
     timings = {}
     for tc in candidates or TILE_CANDIDATES:
         b = lbm.Batch(max_members=len(lats), max_tiles=sum(
-            (lt.n + tc - 1) // tc for lt in lats) + 1, tile_cells=tc, stream=stream)
+            (lt.stored + tc - 1) // tc for lt in lats) + 1, tile_cells=tc, stream=stream)
         for lt in lats:
             b.add(lt, 10 ** 9)
         b.step(2)

@@ -301,7 +301,11 @@ def _row_pair(lattice, shape, storage, walls, tv, steps_chunks, refresh=True):
 @pytest.mark.parametrize("storage", ["fp32", "fp16"])
 @pytest.mark.parametrize("lattice,shape,walls", [
     ("D2Q9", (96, 40, 1), 2), ("D3Q19", (64, 20, 12), 0), ("D3Q19", (64, 18, 14), 6),
-    ("D3Q27", (64, 14, 10), 2), ("D3Q19", (288, 6, 5), 0), ("D3Q27", (320, 5, 6), 4)])
+    ("D3Q27", (64, 14, 10), 2), ("D3Q19", (288, 6, 5), 0), ("D3Q27", (320, 5, 6), 4),
+    # rows that are not a whole number of 32-cell chunks or of 8-element
+    # units (stored rows padded to the next multiple of 8)
+    ("D3Q19", (45, 11, 9), 0), ("D3Q19", (100, 9, 7), 6), ("D2Q9", (77, 30, 1), 2),
+    ("D3Q27", (13, 8, 7), 0), ("D3Q19", (500, 4, 3), 0)])
 def test_row_kernel_matches_cell_kernel_and_oracle(lattice, shape, walls, storage):
     """The row-staged kernel (TMA bulk copies of whole rows) and the
     one-cell-per-thread kernel compute the same update: equal populations to
