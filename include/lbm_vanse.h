@@ -210,6 +210,35 @@ LBM_API int lbm_vanse_step(lbm_vanse_t h, long long max_steps, double residual_t
 LBM_API int lbm_vanse_moments(lbm_vanse_t h, float *rho, float *p, float *u, int on_device);
 LBM_API int lbm_vanse_moments_f64(lbm_vanse_t h, double *rho, double *p, double *u, int on_device);
 
+/* Host copies of rho, p and u, the same values as lbm_vanse_moments with
+   on_device = 0, read back without allocating any device memory.  The paper
+   has no counterpart: this is a library service.
+
+   lbm_vanse_moments stages host outputs in a temporary device buffer.  Some
+   callers cannot allocate one: a server that has handed its whole device
+   memory budget to resident lattices (a temporary buffer could fail with
+   out-of-memory, or hold memory the budget gave to another lattice), or a
+   thread that must not call into the CUDA allocator while other threads use
+   the same memory pool.  This call stages the fields instead in one fixed
+   device array of LBM_NOALLOC_SCRATCH_BYTES that the library reserves when
+   it is loaded on a device.  Each cell needs 20 bytes, so lattices of at
+   most LBM_NOALLOC_MAX_CELLS cells (nx*ny*nz) are accepted; larger ones
+   fail with LBM_EINVAL and a message naming the limit.
+
+   All calls on a device share that array: calls that overlap in time (from
+   several host threads) race on it and may return each other's values, so
+   callers must serialise them.  The call needs nothing in the array to start
+   at zero (every staged value is written before it is read) and returns
+   after the copies to the host have completed.  The first call on a device
+   looks up the array's address there (cudaGetSymbolAddress, with that device
+   current); when that set-up happens in the first call, make that call
+   before any stream capture begins.  rho, p: N values; u: 3*N values; any
+   may be NULL.  Errors: LBM_EINVAL (NULL handle, lattice too large),
+   LBM_ECUDA. */
+#define LBM_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+#define LBM_NOALLOC_MAX_CELLS ((long long)(LBM_NOALLOC_SCRATCH_BYTES / 20))
+LBM_API int lbm_vanse_moments_noalloc(lbm_vanse_t h, float *rho, float *p, float *u);
+
 /* Decoded populations f_i(x, n) in double, natural (not AA-swapped) order,
    array of structures f[cell*Q + i]; host memory.  For checks and dumps. */
 LBM_API int lbm_vanse_get_populations(lbm_vanse_t h, double *f_host);

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -958,3 +959,78 @@ extern "C" int lbm_vanse_set_wait_limit(lbm_vanse_t h, unsigned spins, int withh
 }
 
 extern "C" int lbm_vanse_uses_row_kernel(lbm_vanse_t h) { return h ? (h->ls.row ? 1 : 0) : -1; }
+
+// ---------------------------------------------------------------- read-back without allocation
+
+namespace {
+
+// The staging array of lbm_vanse_moments_noalloc: reserved with the module on
+// every device, shared by all calls on that device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[LBM_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the staging array on `dev`, looked up once per device
+// with that device current.
+int noalloc_scratch(lbm_vanse_t h, int dev, void **out) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    int prev = -1;
+    CUDA_TRY(h, cudaGetDevice(&prev));
+    if (prev != dev) CUDA_TRY(h, cudaSetDevice(dev));
+    void *ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (prev != dev) cudaSetDevice(prev);
+    if (e != cudaSuccess || !ptr)
+      return fail(h, LBM_ECUDA, "address of the staging array on device %d: %s", dev,
+                  cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = ptr;
+  }
+  *out = g_noalloc_ptr[dev];
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" int lbm_vanse_moments_noalloc(lbm_vanse_t h, float *rho, float *p, float *u) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (h->N > LBM_NOALLOC_MAX_CELLS)
+    return fail(h, LBM_EINVAL,
+                "lattice has %lld cells; lbm_vanse_moments_noalloc takes at most %lld (a staging "
+                "array of %zu bytes, 20 bytes per cell)",
+                h->N, (long long)LBM_NOALLOC_MAX_CELLS, (size_t)LBM_NOALLOC_SCRATCH_BYTES);
+  if (!rho && !p && !u) return LBM_OK;
+  // the device that holds the lattice
+  cudaPointerAttributes attr;
+  CUDA_TRY(h, cudaPointerGetAttributes(&attr, h->pop));
+  const int dev = attr.device;
+  if (dev < 0 || dev >= kMaxDevices) return fail(h, LBM_ECUDA, "lattice memory on device %d", dev);
+  int rc;
+  void *scratch = nullptr;
+  if ((rc = noalloc_scratch(h, dev, &scratch))) return rc;
+  int prev = -1;
+  CUDA_TRY(h, cudaGetDevice(&prev));
+  if (prev != dev) CUDA_TRY(h, cudaSetDevice(dev));
+  // rho at 0, p at N, u at 2N floats; the kernel writes every requested value
+  const long long N = h->N;
+  float *srho = static_cast<float *>(scratch), *sp = srho + N, *su = srho + 2 * N;
+  cudaError_t e = cudaSuccess;
+  rc = push_mirror(h);
+  if (rc == LBM_OK) {
+    lbm::count_launches(1);
+    e = lbm::launch_moments(h->h, h->d, h->h.n, nullptr, nullptr, nullptr, rho ? srho : nullptr,
+                            p ? sp : nullptr, u ? su : nullptr, h->stream);
+    if (e == cudaSuccess && rho)
+      e = cudaMemcpyAsync(rho, srho, N * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && p) e = cudaMemcpyAsync(p, sp, N * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && u)
+      e = cudaMemcpyAsync(u, su, 3 * N * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  }
+  if (prev != dev) cudaSetDevice(prev);
+  if (rc) return rc;
+  if (e != cudaSuccess) return fail(h, LBM_ECUDA, "moments_noalloc: %s", cudaGetErrorString(e));
+  return LBM_OK;
+}

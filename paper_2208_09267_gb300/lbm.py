@@ -81,6 +81,7 @@ _SIGS = {
                                       ctypes.POINTER(Stats)]),
     "lbm_vanse_moments": (ctypes.c_int, [_H, _P, _P, _P, ctypes.c_int]),
     "lbm_vanse_moments_f64": (ctypes.c_int, [_H, _P, _P, _P, ctypes.c_int]),
+    "lbm_vanse_moments_noalloc": (ctypes.c_int, [_H, _P, _P, _P]),
     "lbm_vanse_get_populations": (ctypes.c_int, [_H, _P]),
     "lbm_vanse_steps_done": (ctypes.c_longlong, [_H]),
     "lbm_vanse_launch_count": (ctypes.c_longlong, []),
@@ -164,6 +165,11 @@ def _same_device_kind(*items):
 def current_stream_ptr():
     import torch
     return torch.cuda.current_stream().cuda_stream
+
+
+# limits of lbm_vanse_moments_noalloc (its fixed staging array, 20 bytes per cell)
+NOALLOC_SCRATCH_BYTES = 16 << 20
+NOALLOC_MAX_CELLS = NOALLOC_SCRATCH_BYTES // 20
 
 
 def stored_cells(nx: int, ny: int, nz: int) -> int:
@@ -293,6 +299,18 @@ class Lattice:
         u = np.empty(3 * self.n, dt)
         fn = lib().lbm_vanse_moments_f64 if f64 else lib().lbm_vanse_moments
         _check(fn(self.handle, rho.ctypes.data, p.ctypes.data, u.ctypes.data, 0), self.handle)
+        return {"rho": rho, "p": p, "u": u.reshape(3, self.n)}
+
+    def moments_noalloc(self):
+        """dict(rho, p, u) as float32 numpy arrays, read back through the
+        library's fixed staging array instead of a temporary device buffer
+        (lattices of at most NOALLOC_MAX_CELLS cells; concurrent calls from
+        several threads must be serialised by the caller)."""
+        rho = np.empty(self.n, np.float32)
+        p = np.empty(self.n, np.float32)
+        u = np.empty(3 * self.n, np.float32)
+        _check(lib().lbm_vanse_moments_noalloc(self.handle, rho.ctypes.data, p.ctypes.data,
+                                               u.ctypes.data), self.handle)
         return {"rho": rho, "p": p, "u": u.reshape(3, self.n)}
 
     def moments_into(self, rho=None, p=None, u=None):

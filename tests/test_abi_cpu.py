@@ -66,3 +66,14 @@ def test_params_default_and_device_bytes_need_no_gpu():
     assert 19 * n * 4 < b32 < 19 * n * 4 + 3 * n * 4 + (1 << 24)
     assert 19 * n * 2 < b16 < b32
     assert lbm.device_bytes("D2Q9", (4, 4, 2)) == 0  # invalid: D2Q9 needs nz = 1
+
+
+def test_noalloc_limits_match_the_header():
+    """The binding's staging-array limits are the header's."""
+    text = open(os.path.join(ROOT, "include", "lbm_vanse.h")).read()
+    m = re.search(r"#define LBM_NOALLOC_SCRATCH_BYTES \(\(size_t\)(\d+) << (\d+)\)", text)
+    assert m, "LBM_NOALLOC_SCRATCH_BYTES not found"
+    scratch = int(m.group(1)) << int(m.group(2))
+    assert re.search(r"#define LBM_NOALLOC_MAX_CELLS \(\(long long\)\(LBM_NOALLOC_SCRATCH_BYTES / 20\)\)", text)
+    assert lbm.NOALLOC_SCRATCH_BYTES == scratch
+    assert lbm.NOALLOC_MAX_CELLS == scratch // 20
