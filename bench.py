@@ -3,8 +3,9 @@
 Workload (default): D3Q19, 256^3 periodic, FP32 storage, tau = 0.6, body
 force 1e-6 x, space-time varying volume fraction
 phi = 0.7 + 0.2 sin(2 pi x/L) cos(2 pi y/L) sin(2 pi z/L + 2 pi t/T), T = 1000
-steps, refreshed (phi_ref, d_t phi) every 10 steps.  One bench step = one
-fused time step of the whole lattice.  The populations (1.27 GB in FP32) are
+steps, refreshed (phi_ref, d_t phi) every 10 steps, with a check step (FP64
+mass/momentum sums and the velocity residual) every 100 steps.  One bench
+step = one fused time step of the whole lattice.  The populations (1.27 GB in FP32) are
 far larger than L2 (129 MB), so no flush is needed between steps.
 
 Output: one JSON line (rank 0).  ``value`` = GLUPS (10^9 cell updates per
@@ -37,10 +38,12 @@ sys.path.insert(0, ROOT)
 L_DEFAULT = 256
 T_PERIOD = 1000.0
 K_EPS = 10
+K_CHECK = 100  # a check step (FP64 sums, velocity residual) every 100 steps
 TAU = 0.6
 G = (1e-6, 0.0, 0.0)
 Q = 19
-METRIC = "GLUPS (D3Q19 VANSE step, 256^3, FP32)"
+def metric_name(L: int = 256) -> str:
+    return f"GLUPS (D3Q19 VANSE step, {L}^3, FP32)"
 
 
 def bytes_per_cell(storage: str) -> int:
@@ -177,15 +180,17 @@ def run_gpu(args, rank, world):
         done = 0
         while done < steps:
             k = min(K_EPS - (n % K_EPS), steps - done)
+            # plain steps, and a check step where the chunk ends on a multiple of K_CHECK
+            ce = 0 if (n + k) % K_CHECK == 0 else -1
             if timed:
                 a = torch.cuda.Event(enable_timing=True)
                 b = torch.cuda.Event(enable_timing=True)
                 a.record(stream)
-                lat.step(k)
+                lat.step(k, check_every=ce)
                 b.record(stream)
                 ev.append((a, b, k))
             else:
-                lat.step(k)
+                lat.step(k, check_every=ce)
             n += k
             done += k
             if n % K_EPS == 0:
@@ -404,7 +409,7 @@ def main():
         if rank != 0:
             return
         cb = cpu_baseline(sample_L=48 if L >= 48 else L, budget_s=max(5.0, args.steps * 0.5))
-        line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "GLUPS",
+        line = {"impl": "reference", "metric": metric_name(args.size), "value": cb["value"], "unit": "GLUPS",
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic", "config": config, "cpu_baseline": cb,
@@ -426,7 +431,7 @@ def main():
     achieved = bpc * N / (r["kernel_ms"] * 1e-3) / 1e9
     src_hash = kernel_source_hash()
     line = {
-        "metric": METRIC, "value": glups, "unit": "GLUPS", "n_gpus": args.gpus,
+        "metric": metric_name(args.size), "value": glups, "unit": "GLUPS", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["total_ms"] / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if main_st == "fp32" else "f16-storage/f32-compute", "data": "synthetic",

@@ -199,6 +199,10 @@ LBM_API int lbm_vanse_init_equilibrium_f64(lbm_vanse_t h, const double *p0, cons
    residual_tol > 0 and the residual falls to it, the call stops early.
    out (may be NULL) receives the last check's sums.  Synchronises with the
    stream once per check when residual_tol > 0, else once at the end.
+   check_every = -1: no check step at all; the steps are only enqueued on
+   the stream (no synchronisation), out gets steps_done and
+   step_of_stats = -1, and residual_tol must be 0 (a wait-limit timeout in
+   these steps is reported by the next call that checks).
    Errors: LBM_EUNSTABLE when a check saw NaN/Inf (the state is left as it
    is); LBM_ECUDA. */
 LBM_API int lbm_vanse_step(lbm_vanse_t h, long long max_steps, double residual_tol, int check_every,

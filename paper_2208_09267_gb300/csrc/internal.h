@@ -47,6 +47,10 @@ struct LatticeDev {
   double rho0;
   double qw0, qw1;         // Table "weights" row of quad_dim
   float scale, inv_scale;  // 2^k, 2^-k (FP16); 1, 1 otherwise
+  // the parameters above rounded to float once on the host, so the FP32
+  // kernels convert nothing per cell (double conversions run on the narrow
+  // FP64 pipe): rho0, omega, 3 cf, 9 cf, qw0, qw1, g, cf
+  float rho0f, omegaf, cf3f, cf9f, qw0f, qw1f, gf[3], cff;
   // reductions of a check step
   double *partials;        // per-block partial sums, kRedWidth each
   float *u_prev;           // 3*ncell velocity of the previous check, or null

@@ -167,6 +167,15 @@ extern "C" size_t lbm_vanse_device_bytes(const lbm_vanse_params *p, int with_dep
 }
 
 static void sync_mirror_ptrs(lbm_vanse_t h) {
+  LatticeDev &m = h->h;
+  m.rho0f = (float)m.rho0;
+  m.omegaf = (float)m.omega;
+  m.cf3f = 3.0f * (float)m.cf;
+  m.cf9f = 9.0f * (float)m.cf;
+  m.qw0f = (float)m.qw0;
+  m.qw1f = (float)m.qw1;
+  for (int a = 0; a < 3; ++a) m.gf[a] = (float)m.g[a];
+  m.cff = (float)m.cf;
   h->h.pop = h->pop;
   h->h.eps = h->eps_buf[h->eps_cur];
   h->h.deps = h->h.has_deps ? h->deps : nullptr;
@@ -679,12 +688,22 @@ extern "C" int lbm_vanse_step(lbm_vanse_t h, long long max_steps, double residua
                               lbm_vanse_stats *out) {
   if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
   if (max_steps < 0) return fail(h, LBM_EINVAL, "max_steps must be >= 0");
-  if (check_every < 0) return fail(h, LBM_EINVAL, "check_every must be >= 0");
+  if (check_every < -1) return fail(h, LBM_EINVAL, "check_every must be >= -1");
   if (!(residual_tol >= 0.0)) return fail(h, LBM_EINVAL, "residual_tol must be >= 0");
+  if (check_every == -1 && residual_tol > 0.0)
+    return fail(h, LBM_EINVAL, "residual_tol needs check steps (check_every >= 0)");
   int rc;
   lbm_vanse_stats st;
   memset(&st, 0, sizeof(st));
   st.residual = -1.0;
+  if (check_every == -1) {
+    // plain steps only: no reductions and no synchronisation
+    if ((rc = run_steps(h, max_steps))) return rc;
+    st.steps_done = h->h.n;
+    st.step_of_stats = -1;
+    if (out) *out = st;
+    return LBM_OK;
+  }
   if (max_steps == 0) {
     st.steps_done = h->h.n;
     st.step_of_stats = -1;

@@ -148,7 +148,7 @@ __device__ __forceinline__ void update_cell_fast(const LatticeDev &L, long long 
   ST *__restrict__ pop = static_cast<ST *>(L.pop);
   const __half *__restrict__ srd = L.sig_rd;
   const __half *__restrict__ swr = L.sig_wr;
-  const float rho0 = (float)L.rho0;
+  const float rho0 = L.rho0f;
   const float inv_scale = L.inv_scale, scale = L.scale;
   const float s_x = rho0 * __half2float(srd[cell]);
 
@@ -210,14 +210,14 @@ __device__ __forceinline__ void update_cell_fast(const LatticeDev &L, long long 
   if (qa & 1u) nb += e_xp + e_xm;
   if (qa & 2u) nb += e_yp + e_ym;
   if (qa & 4u) nb += e_zp + e_zm;
-  const float I = (float)L.qw0 * e_c + (float)L.qw1 * nb;
+  const float I = L.qw0f * e_c + L.qw1f * nb;
   const float rho = M0 / I;
 
   // 5. eq. (pressForce) plus the external force density
   const float pc = rho * (1.0f / 3.0f);
-  float F0 = (float)L.g[0] + pc * 0.5f * (e_xp - e_xm);
-  float F1 = (float)L.g[1] + pc * 0.5f * (e_yp - e_ym);
-  float F2 = D == 3 ? (float)L.g[2] + pc * 0.5f * (e_zp - e_zm) : 0.f;
+  float F0 = L.gf[0] + pc * 0.5f * (e_xp - e_xm);
+  float F1 = L.gf[1] + pc * 0.5f * (e_yp - e_ym);
+  float F2 = D == 3 ? L.gf[2] + pc * 0.5f * (e_zp - e_zm) : 0.f;
   if (L.has_force) {
     const float *__restrict__ fo = static_cast<const float *>(L.force);
     const long long N = L.ncell;
@@ -269,7 +269,7 @@ __device__ __forceinline__ void update_cell_fast(const LatticeDev &L, long long 
   }
 
   // 7. collide (deviation form) and 8. stream
-  const float omega = (float)L.omega, cf = (float)L.cf;
+  const float omega = L.omegaf, cf = L.cff;
   const bool reshift = srd != swr;
   SRng rng((unsigned)cell, n);
   const bool sr = L.fp16_nearest == 0;

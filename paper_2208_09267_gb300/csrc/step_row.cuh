@@ -16,9 +16,10 @@
 // mbarrier per stage.  Updated populations are written straight to global
 // memory (coalesced, in place, AA pattern).
 //
-// Requirements (checked by the host before choosing this kernel): nx *
-// sizeof(storage) and nx * 4 are multiples of 16 bytes, nx <= 512, walls
-// only on y and/or z.  Every wait is bounded: a block that waits too long
+// Requirements (checked by the host before choosing this kernel): rows
+// stored at a pitch nxp that is a multiple of 8 elements (so every copy
+// starts and ends on a 16-byte boundary), nxp <= 512, fewer than 2^31 stored
+// cells, walls only on y and/or z.  Every wait is bounded: a block that waits too long
 // records the failure in L.status, drains its copies (again bounded) and
 // leaves; the host reports LBM_ETIMEOUT.
 #pragma once
@@ -31,10 +32,13 @@
 
 namespace lbm {
 
-constexpr int kConsumerWarps = 7;
-constexpr int kRowBlock = (kConsumerWarps + 1) * 32;  // + one producer warp: 8 warps, so two
-                                                      // blocks give every SM sub-partition
-                                                      // four warps and 128 registers each
+#ifndef LBM_ROW_CONSUMERS
+#define LBM_ROW_CONSUMERS 7
+#endif
+// consumer warps per block; + one producer warp.  With 7, two blocks give
+// every SM sub-partition four warps and 128 registers each.
+constexpr int kConsumerWarps = LBM_ROW_CONSUMERS;
+constexpr int kRowBlock = (kConsumerWarps + 1) * 32;
 constexpr unsigned kWaitSpins = 1u << 22;  // bounded mbarrier wait
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
@@ -124,20 +128,6 @@ struct RowCtx {
   unsigned solid;   // bit (dz+1)*3+(dy+1): that neighbour row is a wall layer
 };
 
-__device__ __forceinline__ RowCtx make_row_ctx(const LatticeDev &L, int y, int z) {
-  RowCtx c;
-  c.solid = 0;
-  for (int dz = -1; dz <= 1; ++dz)
-    for (int dy = -1; dy <= 1; ++dy) {
-      const int yy = wrapi(y + dy, L.ny), zz = wrapi(z + dz, L.nz);
-      c.base[dz + 1][dy + 1] = (zz * L.ny + yy) * L.nxp;
-      const bool sol = ((L.walls & 2u) && (y + dy <= 0 || y + dy >= L.ny - 1)) ||
-                       ((L.walls & 4u) && (z + dz <= 0 || z + dz >= L.nz - 1));
-      if (sol) c.solid |= 1u << ((dz + 1) * 3 + (dy + 1));
-    }
-  return c;
-}
-
 // Offsets (dy, dz) of the 5-point cross rows (2D: e - 1, 0).
 template <class LAT>
 __host__ __device__ constexpr int cross_dy(int e) {
@@ -162,70 +152,100 @@ __device__ __forceinline__ void dir_yz(int i, int &cy, int &cz) {
   }
 }
 
-// Producer warp: issue every bulk copy of a row into `stage`.  Copy j is
-// issued by lane j % 32; each lane computes its copy's source, destination
-// and size, then the whole warp issues one cp.async.bulk per round.
+// One bulk copy of the producer warp, set up once per launch: lane l owns
+// copies l and l + 32 of every row.  Per row only the source row changes.
+struct RowCopy {
+  const char *src;      // field (population plane included) at row base 0
+  const char *src_own;  // population copies: the own-row plane (bounce-back)
+  unsigned dst;         // byte offset in the stage
+  unsigned bytes;       // 0: this lane has no such copy
+  int dy, dz;           // source row offset
+  int esize;            // bytes per element of the field
+  int nb_pop;           // population read from a neighbour row unless that row is solid
+};
+
 template <class LAT, class ST, bool ODD, int PITCH>
-__device__ __forceinline__ void issue_row(const LatticeDev &L, unsigned char *stage, unsigned long long *bar,
-                                          const RowCtx &rc) {
+__device__ __forceinline__ RowCopy make_row_copy(const LatticeDev &L, int j) {
   using Lay = RowLayout<LAT, ST, ODD, PITCH>;
-  const int lane = threadIdx.x & 31;
+  RowCopy c;
   const bool tv = L.has_deps != 0;
-  // whole stored rows (pitch nxp, a multiple of 8 elements: 16-byte sizes)
-  const int nxp = L.nxp;
-  const unsigned pbytes = (unsigned)nxp * (unsigned)sizeof(ST), sbytes = (unsigned)nxp * 2u,
-                 rbytes = (unsigned)nxp * 4u;
   const int nfield = Lay::kEpsRows + (tv ? Lay::kDepsRows : 0);
   const int ncopies = LAT::Q + Lay::kSigRows + nfield;
-  if (lane == 0)
-    mbar_arrive_expect_tx(bar, (unsigned)LAT::Q * pbytes + (unsigned)Lay::kSigRows * sbytes +
-                                   (unsigned)nfield * rbytes);
-  __syncwarp();
-  const char *pop = static_cast<const char *>(L.pop);
-  const long long plane_bytes = L.plane * (long long)sizeof(ST);
-  const unsigned solid = rc.solid;
-  for (int j = lane; j < ncopies; j += 32) {
-    const char *src;
-    unsigned char *dst;
-    unsigned bytes;
-    if (j < LAT::Q) {
-      int cy, cz;
-      dir_yz<LAT>(j, cy, cz);
-      int plane_i = j, dy = 0, dz = 0;
-      if (ODD && j != 0 && !((solid >> ((1 - cz) * 3 + (1 - cy))) & 1u)) {
-        plane_i = opp_of(j);
-        dy = -cy;
-        dz = -cz;
-      }
-      src = pop + plane_i * plane_bytes + (long long)rc.base[dz + 1][dy + 1] * (long long)sizeof(ST);
-      dst = stage + j * Lay::kPopBytes;
-      bytes = pbytes;
-    } else if (j < LAT::Q + Lay::kSigRows) {
-      const int e = j - LAT::Q;
-      const int dy = ODD ? (LAT::D == 2 ? e : e % 3) - 1 : 0;
-      const int dz = ODD ? (LAT::D == 2 ? 0 : e / 3 - 1) : 0;
-      src = reinterpret_cast<const char *>(L.sig_wr + rc.base[dz + 1][dy + 1]);
-      dst = stage + Lay::kSigOff + e * Lay::kSigBytes;
-      bytes = sbytes;
+  // whole stored rows (pitch nxp, a multiple of 8 elements: 16-byte sizes)
+  const unsigned nxp = (unsigned)L.nxp;
+  c.bytes = 0;
+  c.dy = c.dz = 0;
+  c.nb_pop = 0;
+  c.src = c.src_own = nullptr;
+  c.dst = 0;
+  c.esize = 4;
+  if (j >= ncopies) return c;
+  if (j < LAT::Q) {
+    int cy, cz;
+    dir_yz<LAT>(j, cy, cz);
+    const char *pop = static_cast<const char *>(L.pop);
+    const long long plane_bytes = L.plane * (long long)sizeof(ST);
+    c.src_own = pop + j * plane_bytes;
+    if (ODD && j != 0) {
+      c.src = pop + opp_of(j) * plane_bytes;
+      c.dy = -cy;
+      c.dz = -cz;
+      c.nb_pop = 1;
     } else {
-      const int f = j - LAT::Q - Lay::kSigRows;
-      const bool is_deps = f >= Lay::kEpsRows;
-      const int e = is_deps ? f - Lay::kEpsRows : f;
-      const int off = rc.base[cross_dz<LAT>(e) + 1][cross_dy<LAT>(e) + 1];
-      const float *base = static_cast<const float *>(is_deps ? L.deps : L.eps);
-      src = reinterpret_cast<const char *>(base + off);
-      dst = stage + (is_deps ? Lay::kDepsOff : Lay::kEpsOff) + e * Lay::kRowBytes;
-      bytes = rbytes;
+      c.src = c.src_own;
     }
-    bulk_g2s(dst, src, bytes, bar);
+    c.dst = (unsigned)(j * Lay::kPopBytes);
+    c.bytes = nxp * (unsigned)sizeof(ST);
+    c.esize = (int)sizeof(ST);
+  } else if (j < LAT::Q + Lay::kSigRows) {
+    const int e = j - LAT::Q;
+    c.dy = ODD ? (LAT::D == 2 ? e : e % 3) - 1 : 0;
+    c.dz = ODD ? (LAT::D == 2 ? 0 : e / 3 - 1) : 0;
+    c.src = reinterpret_cast<const char *>(L.sig_wr);
+    c.dst = (unsigned)(Lay::kSigOff + e * Lay::kSigBytes);
+    c.bytes = nxp * 2u;
+    c.esize = 2;
+  } else {
+    const int f = j - LAT::Q - Lay::kSigRows;
+    const bool is_deps = f >= Lay::kEpsRows;
+    const int e = is_deps ? f - Lay::kEpsRows : f;
+    c.dy = cross_dy<LAT>(e);
+    c.dz = cross_dz<LAT>(e);
+    c.src = static_cast<const char *>(is_deps ? L.deps : L.eps);
+    c.dst = (unsigned)((is_deps ? Lay::kDepsOff : Lay::kEpsOff) + e * Lay::kRowBytes);
+    c.bytes = nxp * 4u;
+    c.esize = 4;
   }
+  return c;
+}
+
+// Is row (y, z) a wall layer?
+__device__ __forceinline__ bool wall_row(unsigned walls, int y, int z, int ny, int nz) {
+  return ((walls & 2u) && (y <= 0 || y >= ny - 1)) || ((walls & 4u) && (z <= 0 || z >= nz - 1));
+}
+
+// Issue copy c of row (y, z) into `stage`, completing on `bar`.
+__device__ __forceinline__ void issue_copy(const RowCopy &c, unsigned char *stage, unsigned long long *bar,
+                                           int y, int z, int ny, int nz, int nxp, unsigned walls) {
+  if (!c.bytes) return;
+  int dy = c.dy, dz = c.dz;
+  const char *src = c.src;
+  if (c.nb_pop && walls && wall_row(walls, y + dy, z + dz, ny, nz)) {
+    // halfway bounce-back: the population comes from the own row
+    dy = 0;
+    dz = 0;
+    src = c.src_own;
+  }
+  const int yy = wrapi(y + dy, ny), zz = wrapi(z + dz, nz);
+  bulk_g2s(stage + c.dst, src + (long long)((zz * ny + yy) * nxp) * c.esize, c.bytes, bar);
 }
 
 // Update the 32-cell chunk [x0, x0 + 32) of one staged row (one cell per
 // lane).
 template <class LAT, class ST, bool ODD, bool RED, bool WALLS, int PITCH>
 __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsigned char *stage,
-                                                 const RowCtx &rc, long long n, int x, RedAcc &acc) {
+                                                 const RowCtx &rc, long long n, float dn, float dn_force,
+                                                 int x, RedAcc &acc) {
   using Lay = RowLayout<LAT, ST, ODD, PITCH>;
   constexpr int Q = LAT::Q, D = LAT::D;
   constexpr bool kScaled = sizeof(ST) < 4;  // FP16 stores deviations times 2^k
@@ -235,16 +255,15 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
   const float *erow = reinterpret_cast<const float *>(stage + Lay::kEpsOff);
   const float *drow = reinterpret_cast<const float *>(stage + Lay::kDepsOff);
   const bool tv = L.has_deps != 0;
-  const float dn = (float)(n - L.n_eps);
-  const float rho0 = (float)L.rho0;
+  const float rho0 = L.rho0f;
   const float inv_scale = L.inv_scale, scale = L.scale;
   const __half *__restrict__ srd = L.sig_rd;
   const bool reshift = srd != L.sig_wr;  // shift changed by the last set_epsilon
   ST *__restrict__ pop = static_cast<ST *>(L.pop);
   const int plane = (int)L.plane;
-  const float omega = (float)L.omega;
+  const float omega = L.omegaf;
   const float om1 = 1.0f - omega;
-  const float cf3 = 3.0f * (float)L.cf, cf9 = 9.0f * (float)L.cf;
+  const float cf3 = L.cf3f, cf9 = L.cf9f;
   const unsigned qa = L.quad_axes;
 
 #define EPS_AT(dy, dz, xx) erow[cross_index<LAT>((dy), (dz)) * PITCH + (xx)]
@@ -321,18 +340,18 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
   if (qa & 1u) nb += e_xp + e_xm;
   if (qa & 2u) nb += e_yp + e_ym;
   if (qa & 4u) nb += e_zp + e_zm;
-  const float I = fmaf((float)L.qw0, e_c, (float)L.qw1 * nb);
+  const float I = fmaf(L.qw0f, e_c, L.qw1f * nb);
   const float pc2 = M0 / I * (0.5f / 3.0f);  // c_s^2 rho~ / 2
-  float F0 = fmaf(pc2, e_xp - e_xm, (float)L.g[0]);
-  float F1 = fmaf(pc2, e_yp - e_ym, (float)L.g[1]);
-  float F2 = D == 3 ? fmaf(pc2, e_zp - e_zm, (float)L.g[2]) : 0.f;
+  float F0 = fmaf(pc2, e_xp - e_xm, L.gf[0]);
+  float F1 = fmaf(pc2, e_yp - e_ym, L.gf[1]);
+  float F2 = D == 3 ? fmaf(pc2, e_zp - e_zm, L.gf[2]) : 0.f;
   if (L.has_force) {
     const float *__restrict__ fo = static_cast<const float *>(L.force);
     const int N = (int)L.ncell;
     float a0 = __ldg(fo + cell), a1 = __ldg(fo + N + cell), a2 = D == 3 ? __ldg(fo + 2 * N + cell) : 0.f;
     if (L.has_dforce) {
       const float *__restrict__ df = static_cast<const float *>(L.dforce);
-      const float dnf = (float)(n - L.n_force);
+      const float dnf = dn_force;
       a0 = fmaf(dnf, __ldg(df + cell), a0);
       a1 = fmaf(dnf, __ldg(df + N + cell), a1);
       if (D == 3) a2 = fmaf(dnf, __ldg(df + 2 * N + cell), a2);
@@ -453,9 +472,11 @@ __device__ __forceinline__ bool mbar_wait_or_abort(unsigned long long *bar, unsi
 // Warp-specialised row kernel.  Warp kConsumerWarps is the producer: it
 // stages row j into stage j % NSTAGE once the consumers have released the
 // row that used it before (empty barrier), arming the full barrier with the
-// byte count of the copies.  The consumer warps wait on the full barrier,
-// update their cells and release the stage, one arrival per warp.  No
-// block-wide barrier is taken inside the loop.
+// byte count of the copies.  Each producer lane owns two of the row's copies,
+// set up once per launch, so staging a row costs a few instructions per lane
+// besides the copies.  The consumer warps wait on the full barrier, update
+// their cells and release the stage, one arrival per warp.  No block-wide
+// barrier is taken inside the loop.
 template <class LAT, class ST, bool ODD, bool RED, bool WALLS, int PITCH, int NSTAGE, int MINB>
 __global__ void __launch_bounds__(kRowBlock, MINB) step_row_kernel(const LatticeDev *__restrict__ Lp, int k) {
   using Lay = RowLayout<LAT, ST, ODD, PITCH>;
@@ -494,6 +515,17 @@ __global__ void __launch_bounds__(kRowBlock, MINB) step_row_kernel(const Lattice
   if (warp == kConsumerWarps) {
     // ---------------- producer warp
     const bool withhold = L.withhold_copies != 0;
+    const int ny = L.ny, nz = L.nz, nxp = L.nxp;
+    const unsigned walls = L.walls;
+    const RowCopy c0 = make_row_copy<LAT, ST, ODD, PITCH>(L, lane);
+    const RowCopy c1 = make_row_copy<LAT, ST, ODD, PITCH>(L, lane + 32);
+    const unsigned row_bytes = (unsigned)__reduce_add_sync(0xffffffffu, c0.bytes + c1.bytes);
+    // row r = blockIdx.x + j * gridDim.x is (y0 + r % nyf, z0 + r / nyf); the
+    // step from one row of the block to the next is carried incrementally
+    const int step_y = (int)(gridDim.x % (unsigned)nyf), step_z = (int)(gridDim.x / (unsigned)nyf);
+    int ry = (int)(blockIdx.x % (unsigned)nyf), rz = (int)(blockIdx.x / (unsigned)nyf);
+    // lanes 0..8: the row context entry (dy, dz) = (lane % 3 - 1, lane / 3 - 1)
+    const int cdy = lane % 3 - 1, cdz = lane / 3 - 1;
     int issued_upto = -1;  // last row index j whose copies were issued
     int j = 0;
     for (int r = blockIdx.x; r < nrows; r += gridDim.x, ++j) {
@@ -508,13 +540,27 @@ __global__ void __launch_bounds__(kRowBlock, MINB) step_row_kernel(const Lattice
           break;
         }
       }
-      if (lane == 0) ctx[s] = make_row_ctx(L, y0 + r % nyf, z0 + r / nyf);
+      const int y = y0 + ry, z = z0 + rz;
+      const bool sol = lane < 9 && wall_row(walls, y + cdy, z + cdz, ny, nz);
+      const unsigned solid = __ballot_sync(0xffffffffu, sol) & 0x1ffu;
+      if (lane < 9) ctx[s].base[cdz + 1][cdy + 1] = (wrapi(z + cdz, nz) * ny + wrapi(y + cdy, ny)) * nxp;
+      if (lane == 0) ctx[s].solid = solid;
       __syncwarp();
       if (!withhold) {
-        issue_row<LAT, ST, ODD, PITCH>(L, stages + s * Lay::kStageBytes, &full[s], ctx[s]);
+        if (lane == 0) mbar_arrive_expect_tx(&full[s], row_bytes);
+        __syncwarp();
+        unsigned char *stage = stages + s * Lay::kStageBytes;
+        issue_copy(c0, stage, &full[s], y, z, ny, nz, nxp, walls);
+        issue_copy(c1, stage, &full[s], y, z, ny, nz, nxp, walls);
         issued_upto = j;
       }
       __syncwarp();
+      ry += step_y;
+      rz += step_z;
+      if (ry >= nyf) {
+        ry -= nyf;
+        ++rz;
+      }
     }
     if (abort_flag && lane == 0) {
       // drain: wait (full limit) for every stage whose copies may be in flight
@@ -524,6 +570,8 @@ __global__ void __launch_bounds__(kRowBlock, MINB) step_row_kernel(const Lattice
   } else {
     // ---------------- consumer warps
     const long long n = L.n + k;
+    // steps since the phi and force references, converted once per launch
+    const float dn = (float)(n - L.n_eps), dn_force = (float)(n - L.n_force);
     int j = 0;
     for (int r = blockIdx.x; r < nrows; r += gridDim.x, ++j) {
       const int s = j % NSTAGE;
@@ -539,8 +587,8 @@ __global__ void __launch_bounds__(kRowBlock, MINB) step_row_kernel(const Lattice
       const int nchunks = (L.nx + 31) >> 5;
       const int first = (warp - (int)(((long long)j * nchunks) % kConsumerWarps) + kConsumerWarps) % kConsumerWarps;
       for (int c = first; c < nchunks; c += kConsumerWarps)
-        update_row_chunk<LAT, ST, ODD, RED, WALLS, PITCH>(L, stages + s * Lay::kStageBytes, ctx[s], n,
-                                                          (c << 5) + lane, acc);
+        update_row_chunk<LAT, ST, ODD, RED, WALLS, PITCH>(L, stages + s * Lay::kStageBytes, ctx[s], n, dn,
+                                                          dn_force, (c << 5) + lane, acc);
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[s]);
     }
@@ -622,6 +670,7 @@ int configure_row_v(int &occ) {
 template <class LAT, class ST, int MINB>
 int plan_row_t(int nx, int nxp, int ny, int nz, unsigned walls, StepLaunch &ls) {
   if (nxp % 8 != 0 || nxp > 512 || nx < 8) return 0;
+  if ((long long)nxp * ny * nz > 0x7fffffffLL) return 0;  // int cell indices
   if (walls & 1u) return 0;
   const bool w = (walls & 6u) != 0, p512 = nxp > 256;
   int occ = 0, ok;

@@ -224,6 +224,29 @@ def test_checks_report_mass_and_momentum_balance(storage):
         assert abs(dmom - expect) <= 1e-4 * max(abs(expect), 1e-12) + tol
 
 
+def test_unchecked_steps_update_like_checked_steps():
+    """check_every = -1 enqueues plain steps only (no reductions, no
+    synchronisation); the update is the one a checked run makes."""
+    out = []
+    for mode in ("checked", "unchecked"):
+        lat = lbm.Lattice("D3Q19", (40, 12, 10), tau=0.6, storage="fp32")
+        lat.set_epsilon(I.eps_product_sine((10, 12, 40), 0.2).ravel())
+        lat.set_force((1e-5, 0, 0))
+        lat.init_equilibrium()
+        if mode == "checked":
+            lat.step(23, check_every=5)
+            st = lat.step(1)
+        else:
+            st0 = lat.step(23, check_every=-1)
+            assert st0["step_of_stats"] == -1 and st0["steps_done"] == 23
+            st = lat.step(1)
+        out.append((lat.populations(), st))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1]["mass"] == out[1][1]["mass"]
+    with pytest.raises(lbm.LbmError):
+        lat.step(4, residual_tol=1e-6, check_every=-1)
+
+
 def test_residual_stops_a_converging_run():
     """A channel flow relaxes to steady state; a residual target stops the
     run early and reports convergence."""
