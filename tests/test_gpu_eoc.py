@@ -1,0 +1,115 @@
+"""Second-order convergence of the CUDA path on the manufactured solutions
+of Sec. 3 (the paper's validation): the experimental order of convergence
+(EOC) of the velocity and pressure errors is two within 0.1, as for the
+oracle (same protocol: integral-mass equilibrium start with the Guo
+half-force shift, exact per-step phi and force for the transient example,
+pressure compared after removing the domain means)."""
+import numpy as np
+import pytest
+
+from conftest import golden
+from paper_2208_09267_gb300 import inputs as I
+from paper_2208_09267_gb300 import lbm
+
+pytestmark = pytest.mark.gpu
+
+EOC_TOL = 0.1
+
+
+def _golden_eoc():
+    with open(golden("mms_setup.txt")) as fh:
+        for line in fh:
+            if line.startswith("eoc"):
+                return float(line.split()[1])
+    raise AssertionError("eoc missing from golden file")
+
+
+def run_mms_gpu(example, N, t_end, storage, lattice=None, chunk=8192):
+    import torch
+    m = I.MMS(example, N)
+    lat_name = lattice or m.lattice
+    nz, ny, nx = m.shape
+    lat = lbm.Lattice(lat_name, (nx, ny, nz), tau=m.tau, storage=storage, quad_axes=m.quad_axes)
+    f0 = m.lattice_fields(0)
+    lat.set_epsilon(f0["eps"].ravel(), f64=True)
+    lat.set_force((0, 0, 0), f0["force"].reshape(3, -1), f64=True)
+    lat.init_equilibrium(p0=f0["p"].ravel(), u0=f0["u"].reshape(3, -1), integral=True,
+                         half_force=True, f64=True)
+    nsteps = m.steps_for(t_end)
+    if m.stationary:
+        lat.step(nsteps, check_every=-1)
+    else:
+        # phi and the manufactured force of every step, resident on the device
+        dt = torch.float64 if storage == "fp64" else torch.float32
+        n = 0
+        while n < nsteps:
+            k = min(chunk, nsteps - n)
+            es, fs = m.lattice_series(n, k)
+            es_d = torch.as_tensor(es, dtype=dt).cuda()
+            fs_d = torch.as_tensor(fs.reshape(k, -1), dtype=dt).cuda()
+            for j in range(k):
+                lat.set_epsilon(es_d[j], n_ref=n + j)
+                lat.set_force((0, 0, 0), fs_d[j], n_ref=n + j)
+                lat.step(1, check_every=-1)
+            n += k
+        torch.cuda.synchronize()
+    fl = m.lattice_fields(nsteps)
+    # the moments at the final time use phi and the force of that time
+    lat.set_epsilon(fl["eps"].ravel(), n_ref=nsteps, f64=True)
+    lat.set_force((0, 0, 0), fl["force"].reshape(3, -1), n_ref=nsteps, f64=True)
+    mo = lat.moments()
+    lat.close()
+    d = m.dim
+    vel = m.dx / m.dt
+    pres = (m.dx / m.dt) ** 2
+    u = mo["u"].reshape((3,) + m.shape)[:d]
+    eu = I.error_norms(u * vel, fl["u"][:d] * vel)
+    p = (mo["p"] - mo["p"].mean()) * pres
+    pr = (fl["p"].ravel() - fl["p"].mean()) * pres
+    ep = I.error_norms(p, pr)
+    return eu, ep
+
+
+def _eoc(coarse, fine):
+    return {k: float(np.log2(coarse[k] / fine[k])) for k in coarse}
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp64"])
+def test_stationary_2d_example_eoc_on_the_gpu(storage):
+    """Example 1 on D2Q9 (tau = 0.53), N = 32 -> 64: every norm of u and p."""
+    target = _golden_eoc()
+    eu1, ep1 = run_mms_gpu(1, 32, 15.0, storage)
+    eu2, ep2 = run_mms_gpu(1, 64, 15.0, storage)
+    for name, e in (("u", _eoc(eu1, eu2)), ("p", _eoc(ep1, ep2))):
+        for norm, v in e.items():
+            assert abs(v - target) < EOC_TOL, (storage, name, norm, v)
+
+
+def test_transient_1d_example_eoc_on_the_gpu():
+    """Example 3 on an N x 1 D2Q9 lattice (D1Q3 quadrature, tau = 0.5075),
+    N = 32 -> 64, phi and force replaced every step, FP64 storage.
+
+    FP32 storage does not resolve this case: at N = 64 the run takes 491,520
+    steps in diffusive scaling and the lattice pressure is O(1e-7), so the
+    rounding of the FP32 deviations (about 1e-10 per step, accumulating as a
+    random walk over 5e5 steps) reaches the size of the discretisation error
+    (FP32 orders: u 2.0 (L1) / 2.3 (L2), p 1.0 (L1)).  The FP64 path is the
+    one for such runs."""
+    target = _golden_eoc()
+    eu1, ep1 = run_mms_gpu(3, 32, 12.0, "fp64")
+    eu2, ep2 = run_mms_gpu(3, 64, 12.0, "fp64")
+    for name, e in (("u", _eoc(eu1, eu2)), ("p", _eoc(ep1, ep2))):
+        for norm, v in e.items():
+            assert abs(v - target) < EOC_TOL, (name, norm, v)
+
+
+@pytest.mark.parametrize("lattice", ["D3Q19", "D3Q27"])
+def test_stationary_example_eoc_on_3d_lattices_on_the_gpu(lattice):
+    """Example 1 on one z-layer of a 3D lattice, FP32 storage, N = 16 -> 32:
+    L1 and L2 orders of u and p."""
+    target = _golden_eoc()
+    eu1, ep1 = run_mms_gpu(1, 16, 15.0, "fp32", lattice=lattice)
+    eu2, ep2 = run_mms_gpu(1, 32, 15.0, "fp32", lattice=lattice)
+    for name, e in (("u", _eoc(eu1, eu2)), ("p", _eoc(ep1, ep2))):
+        for norm in ("L1", "L2"):
+            assert abs(e[norm] - target) < EOC_TOL, (lattice, name, norm, e[norm])
