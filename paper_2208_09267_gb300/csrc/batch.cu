@@ -29,6 +29,18 @@ LatticeDev &handle_mirror_mut(lbm_vanse_t h);
 int handle_push(lbm_vanse_t h);
 cudaStream_t handle_stream(lbm_vanse_t h);
 void set_global_error(const char *msg);
+int sm_count();
+// batched row kernel, one entry per lattice type (batch_row_*.cu); pclass
+// selects the row pitch 64, 128, 256 or 512
+cudaError_t launch_batch_row_d2q9(int, int, const BatchMember *, const int *, const int *, const int2 *, double *,
+                                  int *, int, int, int, int, cudaStream_t);
+cudaError_t launch_batch_row_d3q19(int, int, const BatchMember *, const int *, const int *, const int2 *, double *,
+                                   int *, int, int, int, int, cudaStream_t);
+cudaError_t launch_batch_row_d3q27(int, int, const BatchMember *, const int *, const int *, const int2 *, double *,
+                                   int *, int, int, int, int, cudaStream_t);
+int configure_batch_row_d2q9(int storage, int pclass);
+int configure_batch_row_d3q19(int storage, int pclass);
+int configure_batch_row_d3q27(int storage, int pclass);
 }  // namespace lbm
 
 using namespace lbm;
@@ -37,6 +49,8 @@ namespace {
 
 constexpr int kTypes = 6;  // (lattice 0..2) x (storage fp32, fp16)
 constexpr int kBatchBlock = 256;
+constexpr int kPitchClasses = 4;                     // row pitch 64, 128, 256, 512
+constexpr int kRowClasses = kTypes * kPitchClasses;  // batched row kernel classes
 
 int type_of(int lattice, int storage) { return lattice * 2 + (storage == 2 ? 1 : 0); }
 
@@ -99,16 +113,50 @@ __global__ void batch_advance_kernel(BatchMember *members, const int *nmembers, 
 }
 
 // Per-member sums of its tiles' partials, in tile order.
+// Row members: their sums were accumulated by the batched row kernel.
 __global__ void batch_finalize_kernel(const BatchMember *members, const int *nmembers,
-                                      const double *tile_partials, double *out) {
+                                      const double *tile_partials, const double *member_sums, double *out) {
   const int m = blockIdx.x;
   if (m >= *nmembers) return;
   const int j = threadIdx.x;
   if (j >= kRedWidth) return;
   const BatchMember &M = members[m];
   double s = 0.0;
-  for (int t = M.tile_begin; t < M.tile_end; ++t) s += tile_partials[(long long)t * kRedWidth + j];
+  if (M.row) {
+    s = member_sums[(long long)m * kRedWidth + j];
+  } else {
+    for (int t = M.tile_begin; t < M.tile_end; ++t) s += tile_partials[(long long)t * kRedWidth + j];
+  }
   out[(long long)m * kRedWidth + j] = s;
+}
+
+cudaError_t launch_row_class(int cls, const BatchMember *members, const int *row_member, const int *row_begin,
+                             const int2 *cls_dev, double *member_sums, int *status, int k, int kmax,
+                             int red, int grid, cudaStream_t s) {
+  const int type = cls / kPitchClasses, pclass = cls % kPitchClasses;
+  const int lattice = type / 2, storage = (type & 1) ? 2 : 1;
+  switch (lattice) {
+    case 0: return launch_batch_row_d2q9(storage, pclass, members, row_member, row_begin, cls_dev, member_sums,
+                                         status, k, kmax, red, grid, s);
+    case 1: return launch_batch_row_d3q19(storage, pclass, members, row_member, row_begin, cls_dev, member_sums,
+                                          status, k, kmax, red, grid, s);
+    case 2: return launch_batch_row_d3q27(storage, pclass, members, row_member, row_begin, cls_dev, member_sums,
+                                          status, k, kmax, red, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Resident blocks x SMs of a row class; 0 when it cannot run.
+int row_class_grid(int cls) {
+  const int type = cls / kPitchClasses, pclass = cls % kPitchClasses;
+  const int lattice = type / 2, storage = (type & 1) ? 2 : 1;
+  int occ = 0;
+  switch (lattice) {
+    case 0: occ = configure_batch_row_d2q9(storage, pclass); break;
+    case 1: occ = configure_batch_row_d3q19(storage, pclass); break;
+    case 2: occ = configure_batch_row_d3q27(storage, pclass); break;
+  }
+  return occ > 0 ? occ * sm_count() : 0;
 }
 
 template <class LAT, class ST>
@@ -141,6 +189,8 @@ struct HostMember {
   lbm_vanse_t h;
   long long budget;
   int type;
+  int row_class;  // batched row kernel class, or -1 (one-cell-per-thread tiles)
+  int nrows;      // fluid rows (row members)
   long long last_check_n;
   bool have_prev;
   double stats[kRedWidth];
@@ -166,6 +216,17 @@ struct lbm_vanse_batch {
   std::vector<BatchMember> members_host;
   std::vector<BatchTile> tiles_host;
   std::vector<BatchRange> ranges_host;
+  // batched row kernel: class row tables, per-member sums, wait status
+  int *row_member_dev = nullptr;
+  long long row_cap = 0;
+  int *row_begin_dev = nullptr;   // max_members
+  int2 *cls_dev = nullptr;        // kRowClasses (first row, rows)
+  double *member_sums = nullptr;  // max_members x kRedWidth
+  int *status_dev = nullptr;
+  int *status_host = nullptr;
+  int class_grid[kRowClasses] = {};  // 0: not configured yet, -1: cannot run
+  std::vector<int> rows_host, row_begin_host;
+  std::vector<int2> cls_host;
 };
 
 static int bfail(int code, const char *msg) {
@@ -196,6 +257,12 @@ extern "C" int lbm_vanse_batch_create(int max_members, int max_tiles, int tile_c
   if (e == cudaSuccess) e = cudaMalloc(&b->tile_partials, sizeof(double) * kRedWidth * max_tiles);
   if (e == cudaSuccess) e = cudaMalloc(&b->out_dev, sizeof(double) * kRedWidth * max_members);
   if (e == cudaSuccess) e = cudaMallocHost(&b->out_host, sizeof(double) * kRedWidth * max_members);
+  if (e == cudaSuccess) e = cudaMalloc(&b->row_begin_dev, sizeof(int) * max_members);
+  if (e == cudaSuccess) e = cudaMalloc(&b->cls_dev, sizeof(int2) * kRowClasses);
+  if (e == cudaSuccess) e = cudaMalloc(&b->member_sums, sizeof(double) * kRedWidth * max_members);
+  if (e == cudaSuccess) e = cudaMalloc(&b->status_dev, sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost(&b->status_host, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(b->status_dev, 0, sizeof(int));
   if (e != cudaSuccess) {
     cudaGetLastError();
     lbm_vanse_batch_destroy(b);
@@ -217,6 +284,12 @@ extern "C" void lbm_vanse_batch_destroy(lbm_vanse_batch_t b) {
   cudaFree(b->tile_partials);
   cudaFree(b->out_dev);
   if (b->out_host) cudaFreeHost(b->out_host);
+  cudaFree(b->row_member_dev);
+  cudaFree(b->row_begin_dev);
+  cudaFree(b->cls_dev);
+  cudaFree(b->member_sums);
+  cudaFree(b->status_dev);
+  if (b->status_host) cudaFreeHost(b->status_host);
   delete b;
 }
 
@@ -232,9 +305,6 @@ extern "C" int lbm_vanse_batch_add(lbm_vanse_batch_t b, lbm_vanse_t h, long long
   for (auto &hm : b->members)
     if (hm.h == h) return bfail(LBM_EINVAL, "lattice is already a member");
   if ((int)b->members.size() >= b->max_members) return bfail(LBM_ENOMEM, "batch member table is full");
-  int used = 0;
-  for (auto &hm : b->members) used += tiles_needed(b, handle_mirror(hm.h).ncell);
-  if (used + tiles_needed(b, m.ncell) > b->max_tiles) return bfail(LBM_ENOMEM, "batch tile table is full");
   // residual tracking needs the previous check's velocity
   LatticeDev &mm = handle_mirror_mut(h);
   if (!mm.u_prev) {
@@ -250,6 +320,31 @@ extern "C" int lbm_vanse_batch_add(lbm_vanse_batch_t b, lbm_vanse_t h, long long
   hm.h = h;
   hm.budget = max_steps;
   hm.type = type_of(m.lattice, m.storage);
+  hm.row_class = -1;
+  // the batched row kernel takes the member unless its lattice was created
+  // for the one-cell-per-thread kernel or its rows do not fit the kernel
+  lbm_vanse_params p;
+  if (lbm_vanse_get_params(h, &p) == LBM_OK && p.kernel != 1 /* one cell per thread */ && m.nx >= 8 &&
+      m.nxp <= 512 && !(m.walls & 1u) && m.ncell <= 0x7fffffffLL) {
+    const int nyf = (m.walls & 2u) ? m.ny - 2 : m.ny, nzf = (m.walls & 4u) ? m.nz - 2 : m.nz;
+    const int pclass = m.nxp <= 64 ? 0 : (m.nxp <= 128 ? 1 : (m.nxp <= 256 ? 2 : 3));
+    const int cls = hm.type * kPitchClasses + pclass;
+    if (b->class_grid[cls] == 0) {
+      const int g = row_class_grid(cls);
+      b->class_grid[cls] = g > 0 ? g : -1;
+    }
+    if (nyf >= 1 && nzf >= 1 && b->class_grid[cls] > 0) {
+      hm.row_class = cls;
+      hm.nrows = nyf * nzf;
+    }
+  }
+  if (hm.row_class < 0) {
+    // one-cell-per-thread members hold tiles of the tile table
+    int used = 0;
+    for (auto &o : b->members)
+      if (o.row_class < 0) used += tiles_needed(b, handle_mirror(o.h).ncell);
+    if (used + tiles_needed(b, m.ncell) > b->max_tiles) return bfail(LBM_ENOMEM, "batch tile table is full");
+  }
   hm.last_check_n = -1;
   hm.stats_n = -1;
   b->members.push_back(hm);
@@ -287,8 +382,9 @@ static int upload_tables(lbm_vanse_batch_t b) {
       bm.budget = hm.budget;
       bm.lattice = m.lattice;
       bm.storage = m.storage;
+      bm.row = hm.row_class >= 0 ? 1 : 0;
       bm.tile_begin = (int)b->tiles_host.size();
-      for (long long c = 0; c < m.ncell; c += b->tile_cells) {
+      for (long long c = 0; !bm.row && c < m.ncell; c += b->tile_cells) {
         BatchTile tl;
         tl.member = i;
         tl.z = 0;
@@ -305,7 +401,47 @@ static int upload_tables(lbm_vanse_batch_t b) {
   b->ntiles = (int)b->tiles_host.size();
   cudaStream_t s = b->stream;
   cudaError_t e = cudaSuccess;
-  if (nm) e = cudaMemcpyAsync(b->members_dev, b->members_host.data(), sizeof(BatchMember) * nm, cudaMemcpyHostToDevice, s);
+  if (b->dirty) {
+    // class row tables: the rows of each class, member after member
+    b->rows_host.clear();
+    b->row_begin_host.assign(nm, 0);
+    b->cls_host.assign(kRowClasses, make_int2(0, 0));
+    for (int c = 0; c < kRowClasses; ++c) {
+      const int base = (int)b->rows_host.size();
+      for (int i = 0; i < nm; ++i) {
+        const HostMember &hm = b->members[i];
+        if (hm.row_class != c) continue;
+        b->row_begin_host[i] = (int)b->rows_host.size() - base;
+        b->rows_host.insert(b->rows_host.end(), (size_t)hm.nrows, i);
+      }
+      b->cls_host[c] = make_int2(base, (int)b->rows_host.size() - base);
+    }
+    const long long nrows = (long long)b->rows_host.size();
+    if (nrows > b->row_cap) {
+      // a new table: graphs that captured the old pointer are dropped
+      if (b->stream) cudaStreamSynchronize(b->stream);
+      else cudaDeviceSynchronize();
+      cudaFree(b->row_member_dev);
+      b->row_member_dev = nullptr;
+      b->row_cap = 0;
+      for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+      b->graphs.clear();
+      const long long cap = nrows + nrows / 2 + 1024;
+      if (cudaMalloc(&b->row_member_dev, sizeof(int) * cap) != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(LBM_ENOMEM, "batch row table allocation failed");
+      }
+      b->row_cap = cap;
+    }
+    if (nrows)
+      e = cudaMemcpyAsync(b->row_member_dev, b->rows_host.data(), sizeof(int) * nrows, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && nm)
+      e = cudaMemcpyAsync(b->row_begin_dev, b->row_begin_host.data(), sizeof(int) * nm, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->cls_dev, b->cls_host.data(), sizeof(int2) * kRowClasses, cudaMemcpyHostToDevice, s);
+  }
+  if (e == cudaSuccess && nm)
+    e = cudaMemcpyAsync(b->members_dev, b->members_host.data(), sizeof(BatchMember) * nm, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && b->ntiles)
     e = cudaMemcpyAsync(b->tiles_dev, b->tiles_host.data(), sizeof(BatchTile) * b->ntiles, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
@@ -319,7 +455,8 @@ static int upload_tables(lbm_vanse_batch_t b) {
   return LBM_OK;
 }
 
-static int batch_graph(lbm_vanse_batch_t b, unsigned types, int k, int red, cudaGraphExec_t *out) {
+// types: bits 0..5 cell-kernel types present, bits 8.. row classes present
+static int batch_graph(lbm_vanse_batch_t b, unsigned long long types, int k, int red, cudaGraphExec_t *out) {
   auto key = std::make_pair(types, (long long)k * 2 + red);
   auto it = b->graphs.find(key);
   if (it != b->graphs.end()) {
@@ -330,18 +467,26 @@ static int batch_graph(lbm_vanse_batch_t b, unsigned types, int k, int red, cuda
   if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return bfail(LBM_ECUDA, "stream create");
   cudaGraph_t g;
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess && red && (types >> 8))
+    e = cudaMemsetAsync(b->member_sums, 0, sizeof(double) * kRedWidth * b->max_members, cs);
   if (e == cudaSuccess) {
-    for (int j = 0; j < k && e == cudaSuccess; ++j)
+    for (int j = 0; j < k && e == cudaSuccess; ++j) {
       for (int t = 0; t < kTypes && e == cudaSuccess; ++t)
-        if (types & (1u << t))
+        if (types & (1ull << t))
           e = launch_batch_type(t, b->members_dev, b->tiles_dev, b->ranges_dev + t, j, k, red,
                                 b->tile_partials, b->grid, cs);
+      for (int c = 0; c < kRowClasses && e == cudaSuccess; ++c)
+        if (types & (1ull << (8 + c)))
+          e = launch_row_class(c, b->members_dev, b->row_member_dev, b->row_begin_dev, b->cls_dev + c,
+                               b->member_sums, b->status_dev, j, k, red, b->class_grid[c], cs);
+    }
     if (e == cudaSuccess) {
       batch_advance_kernel<<<(b->max_members + 127) / 128, 128, 0, cs>>>(b->members_dev, b->nmembers_dev, k);
       e = cudaGetLastError();
     }
     if (red && e == cudaSuccess) {
-      batch_finalize_kernel<<<b->max_members, 32, 0, cs>>>(b->members_dev, b->nmembers_dev, b->tile_partials, b->out_dev);
+      batch_finalize_kernel<<<b->max_members, 32, 0, cs>>>(b->members_dev, b->nmembers_dev, b->tile_partials,
+                                                           b->member_sums, b->out_dev);
       e = cudaGetLastError();
     }
     cudaError_t e2 = cudaStreamEndCapture(cs, &g);
@@ -368,27 +513,34 @@ extern "C" int lbm_vanse_batch_step(lbm_vanse_batch_t b, int k, int check) {
   int rc;
   // members' descriptors must be current on the device (their own streams
   // may have pending uploads): synchronise those streams first
-  unsigned types = 0;
+  unsigned long long types = 0;
   for (auto &hm : b->members) {
     LatticeDev &m = handle_mirror_mut(hm.h);
     m.have_prev = hm.have_prev ? 1 : 0;
     if ((rc = handle_push(hm.h))) return bfail(rc, "member descriptor upload failed");
     cudaStreamSynchronize(handle_stream(hm.h));
-    types |= 1u << hm.type;
+    if (hm.row_class >= 0) types |= 1ull << (8 + hm.row_class);
+    else types |= 1ull << hm.type;
   }
   if ((rc = upload_tables(b))) return rc;
   cudaGraphExec_t ge;
   if ((rc = batch_graph(b, types, k, check ? 1 : 0, &ge))) return rc;
   cudaError_t e = cudaGraphLaunch(ge, b->stream);
   if (e != cudaSuccess) return bfail(LBM_ECUDA, cudaGetErrorString(e));
-  count_launches((long long)k * __builtin_popcount(types) + 1 + (check ? 1 : 0));
+  count_launches((long long)k * __builtin_popcountll(types) + 1 + (check ? 1 : 0));
   if (check) {
     e = cudaMemcpyAsync(b->out_host, b->out_dev, sizeof(double) * kRedWidth * b->members.size(),
                         cudaMemcpyDeviceToHost, b->stream);
     if (e != cudaSuccess) return bfail(LBM_ECUDA, cudaGetErrorString(e));
   }
-  e = cudaStreamSynchronize(b->stream);
+  e = cudaMemcpyAsync(b->status_host, b->status_dev, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return bfail(LBM_ECUDA, cudaGetErrorString(e));
+  if (*b->status_host) {
+    cudaMemsetAsync(b->status_dev, 0, sizeof(int), b->stream);
+    *b->status_host = 0;
+    return bfail(LBM_ETIMEOUT, "a bounded wait in the batched row kernel gave up");
+  }
   // host mirrors follow the device
   for (size_t i = 0; i < b->members.size(); ++i) {
     HostMember &hm = b->members[i];

@@ -1,0 +1,243 @@
+// batch_row.cuh -- the row-staged fused step (step_row.cuh) over the rows of
+// many lattices in one persistent launch.
+//
+// A batch class is one (lattice, storage, row pitch) combination.  Its rows
+// are the fluid rows of every member of the class, member after member; the
+// class row table maps a row to its member.  Block b stages rows b, b + G,
+// b + 2G, ... (G = grid size) exactly as the single-lattice kernel does, but
+// each row carries its own member: the producer warp looks the member up,
+// copies the member's device descriptor into the stage beside the row's
+// populations and fields, and records in the stage context whether the row
+// is skipped (member's step budget spent), odd or even (each member has its
+// own time) and a check step.  The consumers update the row with the same
+// per-cell code as a lattice stepped alone (update_row_chunk), so a member's
+// populations are bit-identical alone and in any batch.
+//
+// Stage depth follows the row pitch: short rows give small stages, so more
+// rows are in flight per block (up to 12).  Check-step sums are reduced per
+// warp and added into per-member FP64 sums with atomics when the row's
+// member changes (their summation order, not the per-cell values, depends
+// on the schedule).
+#pragma once
+
+#include "step_row.cuh"
+
+namespace lbm {
+
+static_assert(sizeof(LatticeDev) % 16 == 0, "the descriptor is staged by one bulk copy");
+constexpr int kDescBytes = (int)sizeof(LatticeDev);
+
+// Stage context of the batched kernel.
+struct BatchRowCtx {
+  RowCtx rc;
+  int member;  // slot in the member table
+  int flags;   // bit 0: skip, bit 1: odd step, bit 2: check step
+};
+
+template <class LAT, class ST, int P>
+struct BatchRowCfg {
+  static constexpr int kStage = kDescBytes + RowLayout<LAT, ST, true, P>::kStageBytes;
+  static constexpr int kMinB = 2 * kStage <= 110 * 1024 ? 2 : 1;
+  static constexpr int kBudget = kMinB == 2 ? 110 * 1024 : 216 * 1024;
+  static constexpr int kFit = kBudget / kStage;
+  static constexpr int kStages = kFit > 12 ? 12 : kFit;
+};
+
+// Warp sum of acc, added into the member's sums by lane 0; acc is cleared.
+__device__ __forceinline__ void flush_member_sums(RedAcc &acc, double *sums) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < kRedWidth; ++j) {
+    double v = acc.v[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0 && v != 0.0) atomicAdd(sums + j, v);
+    acc.v[j] = 0.0;
+  }
+}
+
+template <class LAT, class ST, int P, int NSTAGE, int MINB>
+__global__ void __launch_bounds__(kRowBlock, MINB)
+    batch_row_kernel(const BatchMember *__restrict__ members, const int *__restrict__ row_member,
+                     const int *__restrict__ row_begin, const int2 *__restrict__ cls,
+                     double *__restrict__ member_sums, int *status, int k, int kmax, int check) {
+  constexpr int kStage = BatchRowCfg<LAT, ST, P>::kStage;
+  __shared__ alignas(8) unsigned long long full[NSTAGE];
+  __shared__ alignas(8) unsigned long long empty[NSTAGE];
+  __shared__ BatchRowCtx ctx[NSTAGE];
+  __shared__ volatile int abort_flag;
+  extern __shared__ __align__(128) unsigned char stages[];
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < NSTAGE; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kConsumerWarps);
+    }
+    abort_flag = 0;
+    mbar_fence_init();
+  }
+  __syncthreads();
+  // the class's rows are row_member[base, base + nrows)
+  const int base = cls->x, nrows = cls->y;
+  const unsigned limit = kWaitSpins;
+
+  if (warp == kConsumerWarps) {
+    // ---------------- producer warp
+    int cur = -1;  // member whose copies c0, c1 are set up
+    RowCopy c0, c1;
+    unsigned row_bytes = 0;
+    int ny = 1, nz = 1, nxp = 8, y0 = 0, z0 = 0, nyf = 1, rb = 0, flags_m = 0;
+    unsigned walls = 0;
+    const LatticeDev *Lg = nullptr;
+    int issued_upto = -1;
+    int j = 0;
+    for (int r = blockIdx.x; r < nrows; r += gridDim.x, ++j) {
+      const int s = j % NSTAGE;
+      if (j >= NSTAGE) {
+        if (!mbar_wait_or_abort(&empty[s], (unsigned)(((j / NSTAGE) - 1) & 1), limit, &abort_flag)) {
+          if (lane == 0 && !abort_flag) {
+            abort_flag = 1;
+            atomicExch(status, 1);
+          }
+          break;
+        }
+      }
+      const int m = row_member[base + r];
+      if (m != cur) {
+        cur = m;
+        const BatchMember &M = members[m];
+        Lg = M.L;
+        const long long budget = M.budget;
+        const long long last = (budget < kmax ? budget : kmax) - 1;
+        rb = row_begin[m];
+        ny = Lg->ny;
+        nz = Lg->nz;
+        nxp = Lg->nxp;
+        walls = Lg->walls;
+        y0 = (walls & 2u) ? 1 : 0;
+        z0 = (walls & 4u) ? 1 : 0;
+        nyf = (walls & 2u) ? ny - 2 : ny;
+        const bool odd = ((Lg->n + k) & 1) != 0;
+        if (odd) {
+          c0 = make_row_copy<LAT, ST, true, P>(*Lg, lane);
+          c1 = make_row_copy<LAT, ST, true, P>(*Lg, lane + 32);
+        } else {
+          c0 = make_row_copy<LAT, ST, false, P>(*Lg, lane);
+          c1 = make_row_copy<LAT, ST, false, P>(*Lg, lane + 32);
+        }
+        row_bytes = (unsigned)__reduce_add_sync(0xffffffffu, c0.bytes + c1.bytes) + (unsigned)kDescBytes;
+        flags_m = (k >= budget ? 1 : 0) | (odd ? 2 : 0) | (check && k == last ? 4 : 0);
+      }
+      const int lr = r - rb;
+      const int y = y0 + lr % nyf, z = z0 + lr / nyf;
+      const int cdy = lane % 3 - 1, cdz = lane / 3 - 1;
+      const bool sol = lane < 9 && wall_row(walls, y + cdy, z + cdz, ny, nz);
+      const unsigned solid = __ballot_sync(0xffffffffu, sol) & 0x1ffu;
+      if (lane < 9) ctx[s].rc.base[cdz + 1][cdy + 1] = (wrapi(z + cdz, nz) * ny + wrapi(y + cdy, ny)) * nxp;
+      if (lane == 0) {
+        ctx[s].rc.solid = solid;
+        ctx[s].member = m;
+        ctx[s].flags = flags_m;
+      }
+      __syncwarp();
+      unsigned char *stage = stages + s * kStage;
+      if (flags_m & 1) {
+        if (lane == 0) mbar_arrive(&full[s]);  // nothing to stage: the phase completes
+      } else {
+        if (lane == 0) {
+          mbar_arrive_expect_tx(&full[s], row_bytes);
+          bulk_g2s(stage, Lg, (unsigned)kDescBytes, &full[s]);
+        }
+        __syncwarp();
+        issue_copy(c0, stage + kDescBytes, &full[s], y, z, ny, nz, nxp, walls);
+        issue_copy(c1, stage + kDescBytes, &full[s], y, z, ny, nz, nxp, walls);
+      }
+      issued_upto = j;
+      __syncwarp();
+    }
+    if (abort_flag && lane == 0) {
+      for (int jj = issued_upto - NSTAGE + 1; jj <= issued_upto; ++jj)
+        if (jj >= 0) mbar_wait_bounded(&full[jj % NSTAGE], (unsigned)((jj / NSTAGE) & 1));
+    }
+  } else {
+    // ---------------- consumer warps
+    RedAcc acc;
+#pragma unroll
+    for (int q = 0; q < kRedWidth; ++q) acc.v[q] = 0.0;
+    int red_m = -1;       // member whose check sums acc holds
+    long long chunk = 0;  // chunks dealt so far (all warps agree)
+    int j = 0;
+    for (int r = blockIdx.x; r < nrows; r += gridDim.x, ++j) {
+      const int s = j % NSTAGE;
+      if (!mbar_wait_or_abort(&full[s], (unsigned)((j / NSTAGE) & 1), limit, &abort_flag)) {
+        if (lane == 0 && !abort_flag) {
+          abort_flag = 1;
+          atomicExch(status, 1);
+        }
+        break;
+      }
+      const int flags = ctx[s].flags;
+      if (!(flags & 1)) {
+        const unsigned char *stage = stages + s * kStage;
+        const LatticeDev &Lm = *reinterpret_cast<const LatticeDev *>(stage);
+        const unsigned char *data = stage + kDescBytes;
+        const int m = ctx[s].member;
+        const bool odd = (flags & 2) != 0, red = (flags & 4) != 0;
+        if (red && m != red_m) {
+          if (red_m >= 0) flush_member_sums(acc, member_sums + (long long)red_m * kRedWidth);
+          red_m = m;
+        }
+        const long long n = Lm.n + k;
+        const float dn = (float)(n - Lm.n_eps), dn_force = (float)(n - Lm.n_force);
+        const int nchunks = (Lm.nx + 31) >> 5;
+        const int first = (int)((warp - chunk % kConsumerWarps + kConsumerWarps) % kConsumerWarps);
+        for (int c = first; c < nchunks; c += kConsumerWarps) {
+          const int x = (c << 5) + lane;
+          if (odd) {
+            if (red) update_row_chunk<LAT, ST, true, true, true, P>(Lm, data, ctx[s].rc, n, dn, dn_force, x, acc);
+            else update_row_chunk<LAT, ST, true, false, true, P>(Lm, data, ctx[s].rc, n, dn, dn_force, x, acc);
+          } else {
+            if (red) update_row_chunk<LAT, ST, false, true, true, P>(Lm, data, ctx[s].rc, n, dn, dn_force, x, acc);
+            else update_row_chunk<LAT, ST, false, false, true, P>(Lm, data, ctx[s].rc, n, dn, dn_force, x, acc);
+          }
+        }
+        chunk += nchunks;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
+    }
+    if (red_m >= 0) flush_member_sums(acc, member_sums + (long long)red_m * kRedWidth);
+  }
+}
+
+// Host side: launch of one class.
+template <class LAT, class ST, int P>
+cudaError_t launch_batch_row_t(const BatchMember *members, const int *row_member, const int *row_begin,
+                               const int2 *cls, double *member_sums, int *status, int k, int kmax,
+                               int check, int grid, cudaStream_t s) {
+  using C = BatchRowCfg<LAT, ST, P>;
+  const int smem = C::kStage * C::kStages;
+  batch_row_kernel<LAT, ST, P, C::kStages, C::kMinB><<<grid, kRowBlock, smem, s>>>(
+      members, row_member, row_begin, cls, member_sums, status, k, kmax, check);
+  return cudaGetLastError();
+}
+
+// Resident blocks per SM of one class (after the shared-memory opt-in); 0
+// on failure.
+template <class LAT, class ST, int P>
+int configure_batch_row_t() {
+  using C = BatchRowCfg<LAT, ST, P>;
+  static_assert(C::kStages >= 2, "a class needs at least two stages");
+  const int smem = C::kStage * C::kStages;
+  auto *fn = batch_row_kernel<LAT, ST, P, C::kStages, C::kMinB>;
+  int occ = 0;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kRowBlock, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return occ;
+}
+
+}  // namespace lbm

@@ -142,6 +142,8 @@ struct BatchMember {
   long long budget;    // steps left at the start of the replay
   int tile_begin, tile_end;
   int lattice, storage;
+  int row;             // 1: stepped by the batched row kernel (sums in the member sums)
+  int pad;
 };
 
 cudaError_t launch_batch_step(int lattice, int storage, const BatchMember *members,
