@@ -1,15 +1,19 @@
 // batch.cu -- many independent lattices advanced by persistent,
-// graph-captured kernels over one device work table.
+// graph-captured kernels over device work tables.
 //
-// The table lists tiles (member, first cell, cell count) grouped by
-// (lattice, storage) type.  For each type present, one persistent kernel of
-// (SM count x resident blocks) blocks strides over that type's tiles and
-// applies the fused step of step_fast.cuh to each cell; each member keeps
+// Members whose rows fit the row-staged kernel are grouped in classes
+// (lattice, storage, row pitch 64/128/256/512, with or without y/z walls);
+// each class has a row table and is stepped by one persistent batched row
+// kernel per step (batch_row.cuh).  Other members (nx < 8, nx > 512, walls
+// on x, or created for the one-cell-per-thread kernel) are listed as tiles
+// (member, first cell, cell count) grouped by (lattice, storage) type and
+// stepped by the tiled one-cell-per-thread kernel below.  Each member keeps
 // its own descriptor (time counter, parity, phi, force), so members of any
 // size, parity and age share one launch.  A replay of k steps is a CUDA
-// graph of k launches per type plus one advance kernel; the tables live in
-// device memory, so members can join and leave (continuous batching)
-// without re-capturing the graph.
+// graph: one chain of k launches per class or type, the chains concurrent
+// (members of different classes are independent), then one advance kernel;
+// the tables live in device memory, so members can join and leave
+// (continuous batching) without re-capturing the graph.
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -30,8 +34,9 @@ int handle_push(lbm_vanse_t h);
 cudaStream_t handle_stream(lbm_vanse_t h);
 void set_global_error(const char *msg);
 int sm_count();
-// batched row kernel, one entry per lattice type (batch_row_*.cu); pclass
-// selects the row pitch 64, 128, 256 or 512
+// batched row kernel, one entry per lattice type (batch_row_*.cu); the
+// shape class selects the row pitch 64, 128, 256 or 512 (bits 0-1) and
+// walls on y/z (bit 2)
 cudaError_t launch_batch_row_d2q9(int, int, const BatchMember *, const int *, const int *, const int2 *, double *,
                                   int *, int, int, int, int, cudaStream_t);
 cudaError_t launch_batch_row_d3q19(int, int, const BatchMember *, const int *, const int *, const int2 *, double *,
@@ -49,7 +54,7 @@ namespace {
 
 constexpr int kTypes = 6;  // (lattice 0..2) x (storage fp32, fp16)
 constexpr int kBatchBlock = 256;
-constexpr int kPitchClasses = 4;                     // row pitch 64, 128, 256, 512
+constexpr int kPitchClasses = 8;                     // row pitch 64/128/256/512, with or without y/z walls
 constexpr int kRowClasses = kTypes * kPitchClasses;  // batched row kernel classes
 
 int type_of(int lattice, int storage) { return lattice * 2 + (storage == 2 ? 1 : 0); }
@@ -225,6 +230,11 @@ struct lbm_vanse_batch {
   int *status_dev = nullptr;
   int *status_host = nullptr;
   int class_grid[kRowClasses] = {};  // 0: not configured yet, -1: cannot run
+  // capture: every class (and cell-kernel type) runs its k steps as its own
+  // chain on a side stream; the chains are independent and run concurrently
+  cudaStream_t side[kTypes + kRowClasses] = {};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[kTypes + kRowClasses] = {};
   std::vector<int> rows_host, row_begin_host;
   std::vector<int2> cls_host;
 };
@@ -263,6 +273,11 @@ extern "C" int lbm_vanse_batch_create(int max_members, int max_tiles, int tile_c
   if (e == cudaSuccess) e = cudaMalloc(&b->status_dev, sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost(&b->status_host, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(b->status_dev, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+  for (int i = 0; i < kTypes + kRowClasses && e == cudaSuccess; ++i) {
+    e = cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join[i], cudaEventDisableTiming);
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     lbm_vanse_batch_destroy(b);
@@ -290,6 +305,11 @@ extern "C" void lbm_vanse_batch_destroy(lbm_vanse_batch_t b) {
   cudaFree(b->member_sums);
   cudaFree(b->status_dev);
   if (b->status_host) cudaFreeHost(b->status_host);
+  for (int i = 0; i < kTypes + kRowClasses; ++i) {
+    if (b->side[i]) cudaStreamDestroy(b->side[i]);
+    if (b->ev_join[i]) cudaEventDestroy(b->ev_join[i]);
+  }
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   delete b;
 }
 
@@ -327,7 +347,7 @@ extern "C" int lbm_vanse_batch_add(lbm_vanse_batch_t b, lbm_vanse_t h, long long
   if (lbm_vanse_get_params(h, &p) == LBM_OK && p.kernel != 1 /* one cell per thread */ && m.nx >= 8 &&
       m.nxp <= 512 && !(m.walls & 1u) && m.ncell <= 0x7fffffffLL) {
     const int nyf = (m.walls & 2u) ? m.ny - 2 : m.ny, nzf = (m.walls & 4u) ? m.nz - 2 : m.nz;
-    const int pclass = m.nxp <= 64 ? 0 : (m.nxp <= 128 ? 1 : (m.nxp <= 256 ? 2 : 3));
+    const int pclass = (m.nxp <= 64 ? 0 : (m.nxp <= 128 ? 1 : (m.nxp <= 256 ? 2 : 3))) | ((m.walls & 6u) ? 4 : 0);
     const int cls = hm.type * kPitchClasses + pclass;
     if (b->class_grid[cls] == 0) {
       const int g = row_class_grid(cls);
@@ -469,16 +489,22 @@ static int batch_graph(lbm_vanse_batch_t b, unsigned long long types, int k, int
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess && red && (types >> 8))
     e = cudaMemsetAsync(b->member_sums, 0, sizeof(double) * kRedWidth * b->max_members, cs);
+  if (e == cudaSuccess) e = cudaEventRecord(b->ev_fork, cs);
   if (e == cudaSuccess) {
-    for (int j = 0; j < k && e == cudaSuccess; ++j) {
-      for (int t = 0; t < kTypes && e == cudaSuccess; ++t)
-        if (types & (1ull << t))
-          e = launch_batch_type(t, b->members_dev, b->tiles_dev, b->ranges_dev + t, j, k, red,
-                                b->tile_partials, b->grid, cs);
-      for (int c = 0; c < kRowClasses && e == cudaSuccess; ++c)
-        if (types & (1ull << (8 + c)))
-          e = launch_row_class(c, b->members_dev, b->row_member_dev, b->row_begin_dev, b->cls_dev + c,
-                               b->member_sums, b->status_dev, j, k, red, b->class_grid[c], cs);
+    // one chain of k launches per cell-kernel type and per row class
+    for (int lane = 0; lane < kTypes + kRowClasses && e == cudaSuccess; ++lane) {
+      const bool cell = lane < kTypes;
+      const int c = cell ? lane : lane - kTypes;
+      if (!(types & (1ull << (cell ? c : 8 + c)))) continue;
+      cudaStream_t ss = b->side[lane];
+      e = cudaStreamWaitEvent(ss, b->ev_fork, 0);
+      for (int j = 0; j < k && e == cudaSuccess; ++j)
+        e = cell ? launch_batch_type(c, b->members_dev, b->tiles_dev, b->ranges_dev + c, j, k, red,
+                                     b->tile_partials, b->grid, ss)
+                 : launch_row_class(c, b->members_dev, b->row_member_dev, b->row_begin_dev, b->cls_dev + c,
+                                    b->member_sums, b->status_dev, j, k, red, b->class_grid[c], ss);
+      if (e == cudaSuccess) e = cudaEventRecord(b->ev_join[lane], ss);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, b->ev_join[lane], 0);
     }
     if (e == cudaSuccess) {
       batch_advance_kernel<<<(b->max_members + 127) / 128, 128, 0, cs>>>(b->members_dev, b->nmembers_dev, k);

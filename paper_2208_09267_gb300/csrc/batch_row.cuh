@@ -1,11 +1,15 @@
 // batch_row.cuh -- the row-staged fused step (step_row.cuh) over the rows of
 // many lattices in one persistent launch.
 //
-// A batch class is one (lattice, storage, row pitch) combination.  Its rows
-// are the fluid rows of every member of the class, member after member; the
-// class row table maps a row to its member.  Block b stages rows b, b + G,
-// b + 2G, ... (G = grid size) exactly as the single-lattice kernel does, but
-// each row carries its own member: the producer warp looks the member up,
+// A batch class is one (lattice, storage, row pitch, walls or none)
+// combination.  Its rows are the fluid rows of every member of the class,
+// member after member; the class row table maps a row to its member.  The
+// rows are dealt to the blocks in runs of up to 8 consecutive rows (block b
+// takes runs b, b + G, b + 2G, ..., G = grid size; shorter runs when the
+// class has few rows, so that every block gets work), so that a block's next
+// row is usually the next row of the same member.  Each row carries its own
+// member: the producer warp looks the member up when the row leaves the
+// current member's row range,
 // copies the member's device descriptor into the stage beside the row's
 // populations and fields, and records in the stage context whether the row
 // is skipped (member's step budget spent), odd or even (each member has its
@@ -34,6 +38,33 @@ struct BatchRowCtx {
   int flags;   // bit 0: skip, bit 1: odd step, bit 2: check step
 };
 
+// Row sequence of a block: runs blockIdx.x, blockIdx.x + G, ... of len
+// rows each (len = nrows / (8 G), clamped to 1..8), cut at nrows.  Producer
+// and consumers walk it identically.
+struct RowRuns {
+  int run, t, nrows, len;
+  __device__ __forceinline__ explicit RowRuns(int n) : run(blockIdx.x), t(0), nrows(n) {
+    const int l = n / (8 * (int)gridDim.x);
+    len = l < 1 ? 1 : (l > 8 ? 8 : l);
+  }
+  // current row, or -1 when the block is done
+  __device__ __forceinline__ int row() {
+    int r = run * len + t;
+    if (r >= nrows && t != 0) {
+      t = 0;
+      run += gridDim.x;
+      r = run * len;
+    }
+    return r < nrows ? r : -1;
+  }
+  __device__ __forceinline__ void next() {
+    if (++t == len) {
+      t = 0;
+      run += gridDim.x;
+    }
+  }
+};
+
 template <class LAT, class ST, int P>
 struct BatchRowCfg {
   static constexpr int kStage = kDescBytes + RowLayout<LAT, ST, true, P>::kStageBytes;
@@ -56,7 +87,7 @@ __device__ __forceinline__ void flush_member_sums(RedAcc &acc, double *sums) {
   }
 }
 
-template <class LAT, class ST, int P, int NSTAGE, int MINB>
+template <class LAT, class ST, int P, bool WALLS, int NSTAGE, int MINB>
 __global__ void __launch_bounds__(kRowBlock, MINB)
     batch_row_kernel(const BatchMember *__restrict__ members, const int *__restrict__ row_member,
                      const int *__restrict__ row_begin, const int2 *__restrict__ cls,
@@ -87,12 +118,14 @@ __global__ void __launch_bounds__(kRowBlock, MINB)
     int cur = -1;  // member whose copies c0, c1 are set up
     RowCopy c0, c1;
     unsigned row_bytes = 0;
-    int ny = 1, nz = 1, nxp = 8, y0 = 0, z0 = 0, nyf = 1, rb = 0, flags_m = 0;
+    int ny = 1, nz = 1, nxp = 8, y0 = 0, z0 = 0, nyf = 1, rb = 0, re = 0, flags_m = 0;
+    int prev_r = -2, y = 0, z = 0;
     unsigned walls = 0;
     const LatticeDev *Lg = nullptr;
     int issued_upto = -1;
+    RowRuns runs(nrows);
     int j = 0;
-    for (int r = blockIdx.x; r < nrows; r += gridDim.x, ++j) {
+    for (int r = runs.row(); r >= 0; runs.next(), r = runs.row(), ++j) {
       const int s = j % NSTAGE;
       if (j >= NSTAGE) {
         if (!mbar_wait_or_abort(&empty[s], (unsigned)(((j / NSTAGE) - 1) & 1), limit, &abort_flag)) {
@@ -103,7 +136,8 @@ __global__ void __launch_bounds__(kRowBlock, MINB)
           break;
         }
       }
-      const int m = row_member[base + r];
+      // the row's member: the current one while r stays in its row range
+      const int m = (r >= rb && r < re) ? cur : row_member[base + r];
       if (m != cur) {
         cur = m;
         const BatchMember &M = members[m];
@@ -118,6 +152,8 @@ __global__ void __launch_bounds__(kRowBlock, MINB)
         y0 = (walls & 2u) ? 1 : 0;
         z0 = (walls & 4u) ? 1 : 0;
         nyf = (walls & 2u) ? ny - 2 : ny;
+        re = rb + nyf * ((walls & 4u) ? nz - 2 : nz);
+        prev_r = -2;
         const bool odd = ((Lg->n + k) & 1) != 0;
         if (odd) {
           c0 = make_row_copy<LAT, ST, true, P>(*Lg, lane);
@@ -129,8 +165,18 @@ __global__ void __launch_bounds__(kRowBlock, MINB)
         row_bytes = (unsigned)__reduce_add_sync(0xffffffffu, c0.bytes + c1.bytes) + (unsigned)kDescBytes;
         flags_m = (k >= budget ? 1 : 0) | (odd ? 2 : 0) | (check && k == last ? 4 : 0);
       }
-      const int lr = r - rb;
-      const int y = y0 + lr % nyf, z = z0 + lr / nyf;
+      if (r == prev_r + 1) {
+        // the next row of the same member
+        if (++y == y0 + nyf) {
+          y = y0;
+          ++z;
+        }
+      } else {
+        const int lr = r - rb;
+        y = y0 + lr % nyf;
+        z = z0 + lr / nyf;
+      }
+      prev_r = r;
       const int cdy = lane % 3 - 1, cdz = lane / 3 - 1;
       const bool sol = lane < 9 && wall_row(walls, y + cdy, z + cdz, ny, nz);
       const unsigned solid = __ballot_sync(0xffffffffu, sol) & 0x1ffu;
@@ -167,8 +213,9 @@ __global__ void __launch_bounds__(kRowBlock, MINB)
     for (int q = 0; q < kRedWidth; ++q) acc.v[q] = 0.0;
     int red_m = -1;       // member whose check sums acc holds
     long long chunk = 0;  // chunks dealt so far (all warps agree)
+    RowRuns runs(nrows);
     int j = 0;
-    for (int r = blockIdx.x; r < nrows; r += gridDim.x, ++j) {
+    for (int r = runs.row(); r >= 0; runs.next(), r = runs.row(), ++j) {
       const int s = j % NSTAGE;
       if (!mbar_wait_or_abort(&full[s], (unsigned)((j / NSTAGE) & 1), limit, &abort_flag)) {
         if (lane == 0 && !abort_flag) {
@@ -195,11 +242,11 @@ __global__ void __launch_bounds__(kRowBlock, MINB)
         for (int c = first; c < nchunks; c += kConsumerWarps) {
           const int x = (c << 5) + lane;
           if (odd) {
-            if (red) update_row_chunk<LAT, ST, true, true, true, P>(Lm, data, ctx[s].rc, n, dn, dn_force, x, acc);
-            else update_row_chunk<LAT, ST, true, false, true, P>(Lm, data, ctx[s].rc, n, dn, dn_force, x, acc);
+            if (red) update_row_chunk<LAT, ST, true, true, WALLS, P>(Lm, data, ctx[s].rc, n, dn, dn_force, x, acc);
+            else update_row_chunk<LAT, ST, true, false, WALLS, P>(Lm, data, ctx[s].rc, n, dn, dn_force, x, acc);
           } else {
-            if (red) update_row_chunk<LAT, ST, false, true, true, P>(Lm, data, ctx[s].rc, n, dn, dn_force, x, acc);
-            else update_row_chunk<LAT, ST, false, false, true, P>(Lm, data, ctx[s].rc, n, dn, dn_force, x, acc);
+            if (red) update_row_chunk<LAT, ST, false, true, WALLS, P>(Lm, data, ctx[s].rc, n, dn, dn_force, x, acc);
+            else update_row_chunk<LAT, ST, false, false, WALLS, P>(Lm, data, ctx[s].rc, n, dn, dn_force, x, acc);
           }
         }
         chunk += nchunks;
@@ -212,25 +259,25 @@ __global__ void __launch_bounds__(kRowBlock, MINB)
 }
 
 // Host side: launch of one class.
-template <class LAT, class ST, int P>
+template <class LAT, class ST, int P, bool WALLS>
 cudaError_t launch_batch_row_t(const BatchMember *members, const int *row_member, const int *row_begin,
                                const int2 *cls, double *member_sums, int *status, int k, int kmax,
                                int check, int grid, cudaStream_t s) {
   using C = BatchRowCfg<LAT, ST, P>;
   const int smem = C::kStage * C::kStages;
-  batch_row_kernel<LAT, ST, P, C::kStages, C::kMinB><<<grid, kRowBlock, smem, s>>>(
+  batch_row_kernel<LAT, ST, P, WALLS, C::kStages, C::kMinB><<<grid, kRowBlock, smem, s>>>(
       members, row_member, row_begin, cls, member_sums, status, k, kmax, check);
   return cudaGetLastError();
 }
 
 // Resident blocks per SM of one class (after the shared-memory opt-in); 0
 // on failure.
-template <class LAT, class ST, int P>
+template <class LAT, class ST, int P, bool WALLS>
 int configure_batch_row_t() {
   using C = BatchRowCfg<LAT, ST, P>;
   static_assert(C::kStages >= 2, "a class needs at least two stages");
   const int smem = C::kStage * C::kStages;
-  auto *fn = batch_row_kernel<LAT, ST, P, C::kStages, C::kMinB>;
+  auto *fn = batch_row_kernel<LAT, ST, P, WALLS, C::kStages, C::kMinB>;
   int occ = 0;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kRowBlock, smem) != cudaSuccess) {

@@ -3,47 +3,47 @@
 
 namespace lbm {
 
-// pclass: row pitch 64, 128, 256, 512 for 0..3
-cudaError_t launch_batch_row_d3q19(int storage, int pclass, const BatchMember *members, const int *row_member,
+// shape class: bits 0-1 row pitch 64, 128, 256, 512; bit 2 walls on y/z
+cudaError_t launch_batch_row_d3q19(int storage, int shape, const BatchMember *members, const int *row_member,
                                   const int *row_begin, const int2 *cls, double *member_sums, int *status,
                                   int k, int kmax, int check, int grid, cudaStream_t s) {
-#define LBM_BR(ST, P) \
-  return launch_batch_row_t<D3Q19, ST, P>(members, row_member, row_begin, cls, member_sums, status, k, kmax, check, grid, s)
-  if (storage == 1) {
-    switch (pclass) {
-      case 0: LBM_BR(float, 64);
-      case 1: LBM_BR(float, 128);
-      case 2: LBM_BR(float, 256);
-      case 3: LBM_BR(float, 512);
-    }
-  } else if (storage == 2) {
-    switch (pclass) {
-      case 0: LBM_BR(__half, 64);
-      case 1: LBM_BR(__half, 128);
-      case 2: LBM_BR(__half, 256);
-      case 3: LBM_BR(__half, 512);
-    }
+#define LBM_BR(ST, P, W) \
+  return launch_batch_row_t<D3Q19, ST, P, W>(members, row_member, row_begin, cls, member_sums, status, k, kmax, check, grid, s)
+#define LBM_BR_SHAPES(ST)           \
+  switch (shape) {                 \
+    case 0: LBM_BR(ST, 64, false);  \
+    case 1: LBM_BR(ST, 128, false); \
+    case 2: LBM_BR(ST, 256, false); \
+    case 3: LBM_BR(ST, 512, false); \
+    case 4: LBM_BR(ST, 64, true);   \
+    case 5: LBM_BR(ST, 128, true);  \
+    case 6: LBM_BR(ST, 256, true);  \
+    case 7: LBM_BR(ST, 512, true);  \
   }
+  if (storage == 1) LBM_BR_SHAPES(float)
+  else if (storage == 2) LBM_BR_SHAPES(__half)
+#undef LBM_BR_SHAPES
 #undef LBM_BR
   return cudaErrorInvalidValue;
 }
 
-int configure_batch_row_d3q19(int storage, int pclass) {
-  if (storage == 1) {
-    switch (pclass) {
-      case 0: return configure_batch_row_t<D3Q19, float, 64>();
-      case 1: return configure_batch_row_t<D3Q19, float, 128>();
-      case 2: return configure_batch_row_t<D3Q19, float, 256>();
-      case 3: return configure_batch_row_t<D3Q19, float, 512>();
-    }
-  } else if (storage == 2) {
-    switch (pclass) {
-      case 0: return configure_batch_row_t<D3Q19, __half, 64>();
-      case 1: return configure_batch_row_t<D3Q19, __half, 128>();
-      case 2: return configure_batch_row_t<D3Q19, __half, 256>();
-      case 3: return configure_batch_row_t<D3Q19, __half, 512>();
-    }
+int configure_batch_row_d3q19(int storage, int shape) {
+#define LBM_CF(ST, P, W) return configure_batch_row_t<D3Q19, ST, P, W>()
+#define LBM_CF_SHAPES(ST)           \
+  switch (shape) {                 \
+    case 0: LBM_CF(ST, 64, false);  \
+    case 1: LBM_CF(ST, 128, false); \
+    case 2: LBM_CF(ST, 256, false); \
+    case 3: LBM_CF(ST, 512, false); \
+    case 4: LBM_CF(ST, 64, true);   \
+    case 5: LBM_CF(ST, 128, true);  \
+    case 6: LBM_CF(ST, 256, true);  \
+    case 7: LBM_CF(ST, 512, true);  \
   }
+  if (storage == 1) LBM_CF_SHAPES(float)
+  else if (storage == 2) LBM_CF_SHAPES(__half)
+#undef LBM_CF_SHAPES
+#undef LBM_CF
   return 0;
 }
 
