@@ -10,10 +10,12 @@
 // stepped by the tiled one-cell-per-thread kernel below.  Each member keeps
 // its own descriptor (time counter, parity, phi, force), so members of any
 // size, parity and age share one launch.  A replay of k steps is a CUDA
-// graph: one chain of k launches per class or type, the chains concurrent
+// graph: one chain of k launches per type and per class part (the members
+// of a class whose time is even, or odd, at the replay start), concurrent
 // (members of different classes are independent), then one advance kernel;
 // the tables live in device memory, so members can join and leave
 // (continuous batching) without re-capturing the graph.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -37,11 +39,11 @@ int sm_count();
 // batched row kernel, one entry per lattice type (batch_row_*.cu); the
 // shape class selects the row pitch 64, 128, 256 or 512 (bits 0-1) and
 // walls on y/z (bit 2)
-cudaError_t launch_batch_row_d2q9(int, int, const BatchMember *, const int *, const int *, const int2 *, double *,
+cudaError_t launch_batch_row_d2q9(int, int, int, int, const BatchMember *, const int *, const int *, const int2 *, double *,
                                   int *, int, int, int, int, cudaStream_t);
-cudaError_t launch_batch_row_d3q19(int, int, const BatchMember *, const int *, const int *, const int2 *, double *,
+cudaError_t launch_batch_row_d3q19(int, int, int, int, const BatchMember *, const int *, const int *, const int2 *, double *,
                                    int *, int, int, int, int, cudaStream_t);
-cudaError_t launch_batch_row_d3q27(int, int, const BatchMember *, const int *, const int *, const int2 *, double *,
+cudaError_t launch_batch_row_d3q27(int, int, int, int, const BatchMember *, const int *, const int *, const int2 *, double *,
                                    int *, int, int, int, int, cudaStream_t);
 int configure_batch_row_d2q9(int storage, int pclass);
 int configure_batch_row_d3q19(int storage, int pclass);
@@ -56,6 +58,8 @@ constexpr int kTypes = 6;  // (lattice 0..2) x (storage fp32, fp16)
 constexpr int kBatchBlock = 256;
 constexpr int kPitchClasses = 8;                     // row pitch 64/128/256/512, with or without y/z walls
 constexpr int kRowClasses = kTypes * kPitchClasses;  // batched row kernel classes
+constexpr int kParts = 2 * kRowClasses;  // class x parity of the member's time at the replay start
+constexpr int kLanes = kTypes + kParts;  // concurrent chains of a replay
 
 int type_of(int lattice, int storage) { return lattice * 2 + (storage == 2 ? 1 : 0); }
 
@@ -135,17 +139,17 @@ __global__ void batch_finalize_kernel(const BatchMember *members, const int *nme
   out[(long long)m * kRedWidth + j] = s;
 }
 
-cudaError_t launch_row_class(int cls, const BatchMember *members, const int *row_member, const int *row_begin,
-                             const int2 *cls_dev, double *member_sums, int *status, int k, int kmax,
-                             int red, int grid, cudaStream_t s) {
+cudaError_t launch_row_class(int cls, int odd, const BatchMember *members, const int *row_member,
+                             const int *row_begin, const int2 *cls_dev, double *member_sums, int *status, int k,
+                             int kmax, int red, int grid, cudaStream_t s) {
   const int type = cls / kPitchClasses, pclass = cls % kPitchClasses;
   const int lattice = type / 2, storage = (type & 1) ? 2 : 1;
   switch (lattice) {
-    case 0: return launch_batch_row_d2q9(storage, pclass, members, row_member, row_begin, cls_dev, member_sums,
+    case 0: return launch_batch_row_d2q9(storage, pclass, odd, red, members, row_member, row_begin, cls_dev, member_sums,
                                          status, k, kmax, red, grid, s);
-    case 1: return launch_batch_row_d3q19(storage, pclass, members, row_member, row_begin, cls_dev, member_sums,
+    case 1: return launch_batch_row_d3q19(storage, pclass, odd, red, members, row_member, row_begin, cls_dev, member_sums,
                                           status, k, kmax, red, grid, s);
-    case 2: return launch_batch_row_d3q27(storage, pclass, members, row_member, row_begin, cls_dev, member_sums,
+    case 2: return launch_batch_row_d3q27(storage, pclass, odd, red, members, row_member, row_begin, cls_dev, member_sums,
                                           status, k, kmax, red, grid, s);
   }
   return cudaErrorInvalidValue;
@@ -195,6 +199,7 @@ struct HostMember {
   long long budget;
   int type;
   int row_class;  // batched row kernel class, or -1 (one-cell-per-thread tiles)
+  int group;      // parity of the member's time when the row tables were built
   int nrows;      // fluid rows (row members)
   long long last_check_n;
   bool have_prev;
@@ -217,7 +222,8 @@ struct lbm_vanse_batch {
   bool dirty = true;
   int ntiles = 0;
   int grid = 0;
-  std::map<std::pair<unsigned, long long>, cudaGraphExec_t> graphs;  // (types mask, k*2+red)
+  // (chains present: one character per lane, k*2+red)
+  std::map<std::pair<std::string, long long>, cudaGraphExec_t> graphs;
   std::vector<BatchMember> members_host;
   std::vector<BatchTile> tiles_host;
   std::vector<BatchRange> ranges_host;
@@ -225,16 +231,16 @@ struct lbm_vanse_batch {
   int *row_member_dev = nullptr;
   long long row_cap = 0;
   int *row_begin_dev = nullptr;   // max_members
-  int2 *cls_dev = nullptr;        // kRowClasses (first row, rows)
+  int2 *cls_dev = nullptr;        // kParts (first row, rows)
   double *member_sums = nullptr;  // max_members x kRedWidth
   int *status_dev = nullptr;
   int *status_host = nullptr;
   int class_grid[kRowClasses] = {};  // 0: not configured yet, -1: cannot run
   // capture: every class (and cell-kernel type) runs its k steps as its own
   // chain on a side stream; the chains are independent and run concurrently
-  cudaStream_t side[kTypes + kRowClasses] = {};
+  cudaStream_t side[kLanes] = {};
   cudaEvent_t ev_fork = nullptr;
-  cudaEvent_t ev_join[kTypes + kRowClasses] = {};
+  cudaEvent_t ev_join[kLanes] = {};
   std::vector<int> rows_host, row_begin_host;
   std::vector<int2> cls_host;
 };
@@ -268,16 +274,12 @@ extern "C" int lbm_vanse_batch_create(int max_members, int max_tiles, int tile_c
   if (e == cudaSuccess) e = cudaMalloc(&b->out_dev, sizeof(double) * kRedWidth * max_members);
   if (e == cudaSuccess) e = cudaMallocHost(&b->out_host, sizeof(double) * kRedWidth * max_members);
   if (e == cudaSuccess) e = cudaMalloc(&b->row_begin_dev, sizeof(int) * max_members);
-  if (e == cudaSuccess) e = cudaMalloc(&b->cls_dev, sizeof(int2) * kRowClasses);
+  if (e == cudaSuccess) e = cudaMalloc(&b->cls_dev, sizeof(int2) * kParts);
   if (e == cudaSuccess) e = cudaMalloc(&b->member_sums, sizeof(double) * kRedWidth * max_members);
   if (e == cudaSuccess) e = cudaMalloc(&b->status_dev, sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost(&b->status_host, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(b->status_dev, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
-  for (int i = 0; i < kTypes + kRowClasses && e == cudaSuccess; ++i) {
-    e = cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join[i], cudaEventDisableTiming);
-  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     lbm_vanse_batch_destroy(b);
@@ -305,7 +307,7 @@ extern "C" void lbm_vanse_batch_destroy(lbm_vanse_batch_t b) {
   cudaFree(b->member_sums);
   cudaFree(b->status_dev);
   if (b->status_host) cudaFreeHost(b->status_host);
-  for (int i = 0; i < kTypes + kRowClasses; ++i) {
+  for (int i = 0; i < kLanes; ++i) {
     if (b->side[i]) cudaStreamDestroy(b->side[i]);
     if (b->ev_join[i]) cudaEventDestroy(b->ev_join[i]);
   }
@@ -425,12 +427,12 @@ static int upload_tables(lbm_vanse_batch_t b) {
     // class row tables: the rows of each class, member after member
     b->rows_host.clear();
     b->row_begin_host.assign(nm, 0);
-    b->cls_host.assign(kRowClasses, make_int2(0, 0));
-    for (int c = 0; c < kRowClasses; ++c) {
+    b->cls_host.assign(kParts, make_int2(0, 0));
+    for (int c = 0; c < kParts; ++c) {
       const int base = (int)b->rows_host.size();
       for (int i = 0; i < nm; ++i) {
         const HostMember &hm = b->members[i];
-        if (hm.row_class != c) continue;
+        if (hm.row_class < 0 || hm.row_class * 2 + hm.group != c) continue;
         b->row_begin_host[i] = (int)b->rows_host.size() - base;
         b->rows_host.insert(b->rows_host.end(), (size_t)hm.nrows, i);
       }
@@ -458,7 +460,7 @@ static int upload_tables(lbm_vanse_batch_t b) {
     if (e == cudaSuccess && nm)
       e = cudaMemcpyAsync(b->row_begin_dev, b->row_begin_host.data(), sizeof(int) * nm, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(b->cls_dev, b->cls_host.data(), sizeof(int2) * kRowClasses, cudaMemcpyHostToDevice, s);
+      e = cudaMemcpyAsync(b->cls_dev, b->cls_host.data(), sizeof(int2) * kParts, cudaMemcpyHostToDevice, s);
   }
   if (e == cudaSuccess && nm)
     e = cudaMemcpyAsync(b->members_dev, b->members_host.data(), sizeof(BatchMember) * nm, cudaMemcpyHostToDevice, s);
@@ -475,34 +477,42 @@ static int upload_tables(lbm_vanse_batch_t b) {
   return LBM_OK;
 }
 
-// types: bits 0..5 cell-kernel types present, bits 8.. row classes present
-static int batch_graph(lbm_vanse_batch_t b, unsigned long long types, int k, int red, cudaGraphExec_t *out) {
-  auto key = std::make_pair(types, (long long)k * 2 + red);
+// lanes: one character per chain ('1' present): kTypes cell-kernel types,
+// then the row-class parts (class * 2 + parity group)
+static int batch_graph(lbm_vanse_batch_t b, const std::string &lanes, int k, int red, cudaGraphExec_t *out) {
+  auto key = std::make_pair(lanes, (long long)k * 2 + red);
   auto it = b->graphs.find(key);
   if (it != b->graphs.end()) {
     *out = it->second;
     return LBM_OK;
   }
+  for (int lane = 0; lane < kLanes; ++lane)
+    if (lanes[lane] == '1' && !b->side[lane]) {
+      if (cudaStreamCreateWithFlags(&b->side[lane], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&b->ev_join[lane], cudaEventDisableTiming) != cudaSuccess)
+        return bfail(LBM_ECUDA, "side stream create");
+    }
   cudaStream_t cs;
   if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return bfail(LBM_ECUDA, "stream create");
   cudaGraph_t g;
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess && red && (types >> 8))
+  if (e == cudaSuccess && red && lanes.find('1', kTypes) != std::string::npos)
     e = cudaMemsetAsync(b->member_sums, 0, sizeof(double) * kRedWidth * b->max_members, cs);
   if (e == cudaSuccess) e = cudaEventRecord(b->ev_fork, cs);
   if (e == cudaSuccess) {
     // one chain of k launches per cell-kernel type and per row class
-    for (int lane = 0; lane < kTypes + kRowClasses && e == cudaSuccess; ++lane) {
+    for (int lane = 0; lane < kLanes && e == cudaSuccess; ++lane) {
+      if (lanes[lane] != '1') continue;
       const bool cell = lane < kTypes;
-      const int c = cell ? lane : lane - kTypes;
-      if (!(types & (1ull << (cell ? c : 8 + c)))) continue;
+      const int c = cell ? lane : lane - kTypes;  // type, or part = class * 2 + parity group
       cudaStream_t ss = b->side[lane];
       e = cudaStreamWaitEvent(ss, b->ev_fork, 0);
       for (int j = 0; j < k && e == cudaSuccess; ++j)
         e = cell ? launch_batch_type(c, b->members_dev, b->tiles_dev, b->ranges_dev + c, j, k, red,
                                      b->tile_partials, b->grid, ss)
-                 : launch_row_class(c, b->members_dev, b->row_member_dev, b->row_begin_dev, b->cls_dev + c,
-                                    b->member_sums, b->status_dev, j, k, red, b->class_grid[c], ss);
+                 : launch_row_class(c / 2, (c + j) & 1, b->members_dev, b->row_member_dev, b->row_begin_dev,
+                                    b->cls_dev + c, b->member_sums, b->status_dev, j, k, red,
+                                    b->class_grid[c / 2], ss);
       if (e == cudaSuccess) e = cudaEventRecord(b->ev_join[lane], ss);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, b->ev_join[lane], 0);
     }
@@ -539,21 +549,30 @@ extern "C" int lbm_vanse_batch_step(lbm_vanse_batch_t b, int k, int check) {
   int rc;
   // members' descriptors must be current on the device (their own streams
   // may have pending uploads): synchronise those streams first
-  unsigned long long types = 0;
+  std::string lanes(kLanes, '0');
   for (auto &hm : b->members) {
     LatticeDev &m = handle_mirror_mut(hm.h);
     m.have_prev = hm.have_prev ? 1 : 0;
     if ((rc = handle_push(hm.h))) return bfail(rc, "member descriptor upload failed");
     cudaStreamSynchronize(handle_stream(hm.h));
-    if (hm.row_class >= 0) types |= 1ull << (8 + hm.row_class);
-    else types |= 1ull << hm.type;
+    if (hm.row_class >= 0) {
+      // members of one class are split by the parity of their time
+      const int g = (int)(m.n & 1);
+      if (g != hm.group) {
+        hm.group = g;
+        b->dirty = true;
+      }
+      lanes[kTypes + hm.row_class * 2 + g] = '1';
+    } else {
+      lanes[hm.type] = '1';
+    }
   }
   if ((rc = upload_tables(b))) return rc;
   cudaGraphExec_t ge;
-  if ((rc = batch_graph(b, types, k, check ? 1 : 0, &ge))) return rc;
+  if ((rc = batch_graph(b, lanes, k, check ? 1 : 0, &ge))) return rc;
   cudaError_t e = cudaGraphLaunch(ge, b->stream);
   if (e != cudaSuccess) return bfail(LBM_ECUDA, cudaGetErrorString(e));
-  count_launches((long long)k * __builtin_popcountll(types) + 1 + (check ? 1 : 0));
+  count_launches((long long)k * (long long)std::count(lanes.begin(), lanes.end(), '1') + 1 + (check ? 1 : 0));
   if (check) {
     e = cudaMemcpyAsync(b->out_host, b->out_dev, sizeof(double) * kRedWidth * b->members.size(),
                         cudaMemcpyDeviceToHost, b->stream);

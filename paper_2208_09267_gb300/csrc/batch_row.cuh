@@ -9,13 +9,15 @@
 // class has few rows, so that every block gets work), so that a block's next
 // row is usually the next row of the same member.  Each row carries its own
 // member: the producer warp looks the member up when the row leaves the
-// current member's row range,
-// copies the member's device descriptor into the stage beside the row's
-// populations and fields, and records in the stage context whether the row
-// is skipped (member's step budget spent), odd or even (each member has its
-// own time) and a check step.  The consumers update the row with the same
-// per-cell code as a lattice stepped alone (update_row_chunk), so a member's
-// populations are bit-identical alone and in any batch.
+// current member's row range, copies the member's device descriptor into
+// the stage beside the row's populations and fields, and records in the
+// stage context whether the row is skipped (member's step budget spent) or
+// a check step.  Members keep their own time: the rows of a class are split
+// by the parity of the member's time at the start of a replay, and each
+// part is stepped by the even or odd instantiation as the steps alternate.
+// The consumers update the row with the same per-cell code as a lattice
+// stepped alone (update_row_chunk), so a member's populations are
+// bit-identical alone and in any batch.
 //
 // Stage depth follows the row pitch: short rows give small stages, so more
 // rows are in flight per block (up to 12).  Check-step sums are reduced per
@@ -35,7 +37,7 @@ constexpr int kDescBytes = (int)sizeof(LatticeDev);
 struct BatchRowCtx {
   RowCtx rc;
   int member;  // slot in the member table
-  int flags;   // bit 0: skip, bit 1: odd step, bit 2: check step
+  int flags;   // bit 0: skip, bit 2: check step
 };
 
 // Row sequence of a block: runs blockIdx.x, blockIdx.x + G, ... of len
@@ -87,7 +89,8 @@ __device__ __forceinline__ void flush_member_sums(RedAcc &acc, double *sums) {
   }
 }
 
-template <class LAT, class ST, int P, bool WALLS, int NSTAGE, int MINB>
+// REDC: a launch of a check replay (rows may carry the check flag)
+template <class LAT, class ST, int P, bool WALLS, bool ODD, bool REDC, int NSTAGE, int MINB>
 __global__ void __launch_bounds__(kRowBlock, MINB)
     batch_row_kernel(const BatchMember *__restrict__ members, const int *__restrict__ row_member,
                      const int *__restrict__ row_begin, const int2 *__restrict__ cls,
@@ -154,16 +157,10 @@ __global__ void __launch_bounds__(kRowBlock, MINB)
         nyf = (walls & 2u) ? ny - 2 : ny;
         re = rb + nyf * ((walls & 4u) ? nz - 2 : nz);
         prev_r = -2;
-        const bool odd = ((Lg->n + k) & 1) != 0;
-        if (odd) {
-          c0 = make_row_copy<LAT, ST, true, P>(*Lg, lane);
-          c1 = make_row_copy<LAT, ST, true, P>(*Lg, lane + 32);
-        } else {
-          c0 = make_row_copy<LAT, ST, false, P>(*Lg, lane);
-          c1 = make_row_copy<LAT, ST, false, P>(*Lg, lane + 32);
-        }
+        c0 = make_row_copy<LAT, ST, ODD, P>(*Lg, lane);
+        c1 = make_row_copy<LAT, ST, ODD, P>(*Lg, lane + 32);
         row_bytes = (unsigned)__reduce_add_sync(0xffffffffu, c0.bytes + c1.bytes) + (unsigned)kDescBytes;
-        flags_m = (k >= budget ? 1 : 0) | (odd ? 2 : 0) | (check && k == last ? 4 : 0);
+        flags_m = (k >= budget ? 1 : 0) | (REDC && check && k == last ? 4 : 0);
       }
       if (r == prev_r + 1) {
         // the next row of the same member
@@ -230,7 +227,7 @@ __global__ void __launch_bounds__(kRowBlock, MINB)
         const LatticeDev &Lm = *reinterpret_cast<const LatticeDev *>(stage);
         const unsigned char *data = stage + kDescBytes;
         const int m = ctx[s].member;
-        const bool odd = (flags & 2) != 0, red = (flags & 4) != 0;
+        const bool red = REDC && (flags & 4) != 0;
         if (red && m != red_m) {
           if (red_m >= 0) flush_member_sums(acc, member_sums + (long long)red_m * kRedWidth);
           red_m = m;
@@ -241,43 +238,51 @@ __global__ void __launch_bounds__(kRowBlock, MINB)
         const int first = (int)((warp - chunk % kConsumerWarps + kConsumerWarps) % kConsumerWarps);
         for (int c = first; c < nchunks; c += kConsumerWarps) {
           const int x = (c << 5) + lane;
-          if (odd) {
-            if (red) update_row_chunk<LAT, ST, true, true, WALLS, P>(Lm, data, ctx[s].rc, n, dn, dn_force, x, acc);
-            else update_row_chunk<LAT, ST, true, false, WALLS, P>(Lm, data, ctx[s].rc, n, dn, dn_force, x, acc);
-          } else {
-            if (red) update_row_chunk<LAT, ST, false, true, WALLS, P>(Lm, data, ctx[s].rc, n, dn, dn_force, x, acc);
-            else update_row_chunk<LAT, ST, false, false, WALLS, P>(Lm, data, ctx[s].rc, n, dn, dn_force, x, acc);
-          }
+          if (red) update_row_chunk<LAT, ST, ODD, REDC, WALLS, P>(Lm, data, ctx[s].rc, n, dn, dn_force, x, acc);
+          else update_row_chunk<LAT, ST, ODD, false, WALLS, P>(Lm, data, ctx[s].rc, n, dn, dn_force, x, acc);
         }
         chunk += nchunks;
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[s]);
     }
-    if (red_m >= 0) flush_member_sums(acc, member_sums + (long long)red_m * kRedWidth);
+    if (REDC && red_m >= 0) flush_member_sums(acc, member_sums + (long long)red_m * kRedWidth);
   }
 }
 
-// Host side: launch of one class.
-template <class LAT, class ST, int P, bool WALLS>
+// Host side: launch of one class part.
+template <class LAT, class ST, int P, bool WALLS, bool ODD, bool REDC>
 cudaError_t launch_batch_row_t(const BatchMember *members, const int *row_member, const int *row_begin,
                                const int2 *cls, double *member_sums, int *status, int k, int kmax,
                                int check, int grid, cudaStream_t s) {
   using C = BatchRowCfg<LAT, ST, P>;
   const int smem = C::kStage * C::kStages;
-  batch_row_kernel<LAT, ST, P, WALLS, C::kStages, C::kMinB><<<grid, kRowBlock, smem, s>>>(
+  batch_row_kernel<LAT, ST, P, WALLS, ODD, REDC, C::kStages, C::kMinB><<<grid, kRowBlock, smem, s>>>(
       members, row_member, row_begin, cls, member_sums, status, k, kmax, check);
   return cudaGetLastError();
 }
 
-// Resident blocks per SM of one class (after the shared-memory opt-in); 0
-// on failure.
 template <class LAT, class ST, int P, bool WALLS>
-int configure_batch_row_t() {
+cudaError_t launch_batch_row_t(bool odd, bool redc, const BatchMember *members, const int *row_member,
+                               const int *row_begin, const int2 *cls, double *member_sums, int *status, int k,
+                               int kmax, int check, int grid, cudaStream_t s) {
+  if (odd) {
+    if (redc) return launch_batch_row_t<LAT, ST, P, WALLS, true, true>(members, row_member, row_begin, cls,
+                                                                        member_sums, status, k, kmax, check, grid, s);
+    return launch_batch_row_t<LAT, ST, P, WALLS, true, false>(members, row_member, row_begin, cls, member_sums,
+                                                               status, k, kmax, check, grid, s);
+  }
+  if (redc) return launch_batch_row_t<LAT, ST, P, WALLS, false, true>(members, row_member, row_begin, cls,
+                                                                       member_sums, status, k, kmax, check, grid, s);
+  return launch_batch_row_t<LAT, ST, P, WALLS, false, false>(members, row_member, row_begin, cls, member_sums,
+                                                              status, k, kmax, check, grid, s);
+}
+
+template <class LAT, class ST, int P, bool WALLS, bool ODD, bool REDC>
+int configure_batch_row_v() {
   using C = BatchRowCfg<LAT, ST, P>;
-  static_assert(C::kStages >= 2, "a class needs at least two stages");
   const int smem = C::kStage * C::kStages;
-  auto *fn = batch_row_kernel<LAT, ST, P, WALLS, C::kStages, C::kMinB>;
+  auto *fn = batch_row_kernel<LAT, ST, P, WALLS, ODD, REDC, C::kStages, C::kMinB>;
   int occ = 0;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kRowBlock, smem) != cudaSuccess) {
@@ -285,6 +290,20 @@ int configure_batch_row_t() {
     return 0;
   }
   return occ;
+}
+
+// Resident blocks per SM of a class: the least over its four instantiations
+// (after the shared-memory opt-in); 0 on failure.
+template <class LAT, class ST, int P, bool WALLS>
+int configure_batch_row_t() {
+  static_assert(BatchRowCfg<LAT, ST, P>::kStages >= 2, "a class needs at least two stages");
+  int occ = configure_batch_row_v<LAT, ST, P, WALLS, false, false>();
+  int o = configure_batch_row_v<LAT, ST, P, WALLS, true, false>();
+  occ = o < occ ? o : occ;
+  o = configure_batch_row_v<LAT, ST, P, WALLS, false, true>();
+  occ = o < occ ? o : occ;
+  o = configure_batch_row_v<LAT, ST, P, WALLS, true, true>();
+  return o < occ ? o : occ;
 }
 
 }  // namespace lbm

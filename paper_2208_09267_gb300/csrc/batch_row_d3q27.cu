@@ -3,12 +3,13 @@
 
 namespace lbm {
 
-// shape class: bits 0-1 row pitch 64, 128, 256, 512; bit 2 walls on y/z
-cudaError_t launch_batch_row_d3q27(int storage, int shape, const BatchMember *members, const int *row_member,
+// shape class: bits 0-1 row pitch 64, 128, 256, 512; bit 2 walls on y/z;
+// odd: the step parity of the launched part; redc: a check replay
+cudaError_t launch_batch_row_d3q27(int storage, int shape, int odd, int redc, const BatchMember *members, const int *row_member,
                                   const int *row_begin, const int2 *cls, double *member_sums, int *status,
                                   int k, int kmax, int check, int grid, cudaStream_t s) {
 #define LBM_BR(ST, P, W) \
-  return launch_batch_row_t<D3Q27, ST, P, W>(members, row_member, row_begin, cls, member_sums, status, k, kmax, check, grid, s)
+  return launch_batch_row_t<D3Q27, ST, P, W>(odd != 0, redc != 0, members, row_member, row_begin, cls, member_sums, status, k, kmax, check, grid, s)
 #define LBM_BR_SHAPES(ST)           \
   switch (shape) {                 \
     case 0: LBM_BR(ST, 64, false);  \
