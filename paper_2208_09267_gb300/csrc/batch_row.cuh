@@ -38,6 +38,7 @@ struct BatchRowCtx {
   RowCtx rc;
   int member;  // slot in the member table
   int flags;   // bit 0: skip, bit 2: check step
+  float dn, dn_force;  // steps since the member's phi and force references
 };
 
 // Row sequence of a block: runs blockIdx.x, blockIdx.x + G, ... of len
@@ -69,7 +70,7 @@ struct RowRuns {
 
 template <class LAT, class ST, int P>
 struct BatchRowCfg {
-  static constexpr int kStage = kDescBytes + RowLayout<LAT, ST, true, P>::kStageBytes;
+  static constexpr int kStage = RowLayout<LAT, ST, true, P>::kStageBytes;
   static constexpr int kMinB = 2 * kStage <= 110 * 1024 ? 2 : 1;
   static constexpr int kBudget = kMinB == 2 ? 110 * 1024 : 216 * 1024;
   static constexpr int kFit = kBudget / kStage;
@@ -99,6 +100,9 @@ __global__ void __launch_bounds__(kRowBlock, MINB)
   __shared__ alignas(8) unsigned long long full[NSTAGE];
   __shared__ alignas(8) unsigned long long empty[NSTAGE];
   __shared__ BatchRowCtx ctx[NSTAGE];
+  // each stage's member descriptor (a named shared array, so that the
+  // consumers' reads of it compile to shared-memory loads)
+  __shared__ alignas(16) LatticeDev descs[NSTAGE];
   __shared__ volatile int abort_flag;
   extern __shared__ __align__(128) unsigned char stages[];
   const int tid = threadIdx.x;
@@ -120,6 +124,7 @@ __global__ void __launch_bounds__(kRowBlock, MINB)
     // ---------------- producer warp
     int cur = -1;  // member whose copies c0, c1 are set up
     RowCopy c0, c1;
+    float dn_m = 0.f, dnf_m = 0.f;
     unsigned row_bytes = 0;
     int ny = 1, nz = 1, nxp = 8, y0 = 0, z0 = 0, nyf = 1, rb = 0, re = 0, flags_m = 0;
     int prev_r = -2, y = 0, z = 0;
@@ -161,6 +166,10 @@ __global__ void __launch_bounds__(kRowBlock, MINB)
         c1 = make_row_copy<LAT, ST, ODD, P>(*Lg, lane + 32);
         row_bytes = (unsigned)__reduce_add_sync(0xffffffffu, c0.bytes + c1.bytes) + (unsigned)kDescBytes;
         flags_m = (k >= budget ? 1 : 0) | (REDC && check && k == last ? 4 : 0);
+        // converted once per member, not per cell
+        const long long n = Lg->n + k;
+        dn_m = (float)(n - Lg->n_eps);
+        dnf_m = (float)(n - Lg->n_force);
       }
       if (r == prev_r + 1) {
         // the next row of the same member
@@ -182,6 +191,8 @@ __global__ void __launch_bounds__(kRowBlock, MINB)
         ctx[s].rc.solid = solid;
         ctx[s].member = m;
         ctx[s].flags = flags_m;
+        ctx[s].dn = dn_m;
+        ctx[s].dn_force = dnf_m;
       }
       __syncwarp();
       unsigned char *stage = stages + s * kStage;
@@ -190,11 +201,11 @@ __global__ void __launch_bounds__(kRowBlock, MINB)
       } else {
         if (lane == 0) {
           mbar_arrive_expect_tx(&full[s], row_bytes);
-          bulk_g2s(stage, Lg, (unsigned)kDescBytes, &full[s]);
+          bulk_g2s(&descs[s], Lg, (unsigned)kDescBytes, &full[s]);
         }
         __syncwarp();
-        issue_copy(c0, stage + kDescBytes, &full[s], y, z, ny, nz, nxp, walls);
-        issue_copy(c1, stage + kDescBytes, &full[s], y, z, ny, nz, nxp, walls);
+        issue_copy(c0, stage, &full[s], y, z, ny, nz, nxp, walls);
+        issue_copy(c1, stage, &full[s], y, z, ny, nz, nxp, walls);
       }
       issued_upto = j;
       __syncwarp();
@@ -209,7 +220,7 @@ __global__ void __launch_bounds__(kRowBlock, MINB)
 #pragma unroll
     for (int q = 0; q < kRedWidth; ++q) acc.v[q] = 0.0;
     int red_m = -1;       // member whose check sums acc holds
-    long long chunk = 0;  // chunks dealt so far (all warps agree)
+    int chunk = 0;  // chunks dealt so far, modulo the consumer warps (all warps agree)
     RowRuns runs(nrows);
     int j = 0;
     for (int r = runs.row(); r >= 0; runs.next(), r = runs.row(), ++j) {
@@ -223,9 +234,8 @@ __global__ void __launch_bounds__(kRowBlock, MINB)
       }
       const int flags = ctx[s].flags;
       if (!(flags & 1)) {
-        const unsigned char *stage = stages + s * kStage;
-        const LatticeDev &Lm = *reinterpret_cast<const LatticeDev *>(stage);
-        const unsigned char *data = stage + kDescBytes;
+        const unsigned char *data = stages + s * kStage;
+        const LatticeDev &Lm = descs[s];
         const int m = ctx[s].member;
         const bool red = REDC && (flags & 4) != 0;
         if (red && m != red_m) {
@@ -233,15 +243,15 @@ __global__ void __launch_bounds__(kRowBlock, MINB)
           red_m = m;
         }
         const long long n = Lm.n + k;
-        const float dn = (float)(n - Lm.n_eps), dn_force = (float)(n - Lm.n_force);
+        const float dn = ctx[s].dn, dn_force = ctx[s].dn_force;
         const int nchunks = (Lm.nx + 31) >> 5;
-        const int first = (int)((warp - chunk % kConsumerWarps + kConsumerWarps) % kConsumerWarps);
+        const int first = (warp - chunk + kConsumerWarps) % kConsumerWarps;
         for (int c = first; c < nchunks; c += kConsumerWarps) {
           const int x = (c << 5) + lane;
           if (red) update_row_chunk<LAT, ST, ODD, REDC, WALLS, P>(Lm, data, ctx[s].rc, n, dn, dn_force, x, acc);
           else update_row_chunk<LAT, ST, ODD, false, WALLS, P>(Lm, data, ctx[s].rc, n, dn, dn_force, x, acc);
         }
-        chunk += nchunks;
+        chunk = (chunk + nchunks) % kConsumerWarps;
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[s]);
