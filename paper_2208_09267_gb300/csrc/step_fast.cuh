@@ -78,7 +78,23 @@ struct SRng {
     s = s * 1664525u + 1013904223u;
     return s >> 19;
   }
+  // 32 random bits (the low half mixed with the high half: an LCG's low
+  // bits alone repeat with short periods)
+  __device__ __forceinline__ unsigned next32() {
+    s = s * 1664525u + 1013904223u;
+    return s ^ (s >> 16);
+  }
 };
+
+// Two values rounded stochastically to half in one conversion (the
+// conversion adds random bits below the kept mantissa and truncates, as
+// half_sr does; 16 random bits per value): lo in the low half of the
+// result, hi in the high half.
+__device__ __forceinline__ unsigned half2_sr(float lo, float hi, unsigned rbits) {
+  unsigned d;
+  asm("cvt.rs.satfinite.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rbits));
+  return d;
+}
 
 // v rounded stochastically to half: add random bits below the half
 // mantissa to the float's magnitude, then truncate toward zero.
@@ -94,6 +110,26 @@ __device__ __forceinline__ void store_pop(ST *p, float v, SRng &rng, bool sr) {
 template <>
 __device__ __forceinline__ void store_pop<__half>(__half *p, float v, SRng &rng, bool sr) {
   *p = sr ? half_sr(v, rng.next13()) : __float2half_rn(v);
+}
+
+// Store two populations (the members of an opposite pair) to their slots.
+template <class ST>
+__device__ __forceinline__ void store_pop_pair(ST *pa, float va, ST *pb, float vb, SRng &rng, bool sr) {
+  PopIO<ST>::st(pa, va);
+  PopIO<ST>::st(pb, vb);
+}
+
+template <>
+__device__ __forceinline__ void store_pop_pair<__half>(__half *pa, float va, __half *pb, float vb, SRng &rng,
+                                                       bool sr) {
+  if (sr) {
+    const unsigned h = half2_sr(va, vb, rng.next32());
+    *pa = __ushort_as_half((unsigned short)(h & 0xffffu));
+    *pb = __ushort_as_half((unsigned short)(h >> 16));
+  } else {
+    *pa = __float2half_rn(va);
+    *pb = __float2half_rn(vb);
+  }
 }
 
 struct Coords {

@@ -291,15 +291,15 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
     const int cx = LAT::c(i, 0), cy = LAT::c(i, 1), cz = LAT::c(i, 2);
     const bool own = OWN_SRC(i);
     const float q = PopIO<ST>::ld(prow + i * PITCH + (own ? x : xs[1 - cx]));
-    const float qs = kScaled ? q * inv_scale : q;
     if (own) {
       delta[i] = 0.f;
-      d[i] = qs;
+      d[i] = kScaled ? q * inv_scale : q;
     } else {
       const float sm =
           reshift ? __half2float(srd[rc.base[1 - cz][1 - cy] + xs[1 - cx]]) : SIG_AT(-cy, -cz, xs[1 - cx]);
       delta[i] = fmaf(rho0, sm, -s_x);
-      d[i] = qs + delta[i];
+      // q 2^-k is exact, so the FMA rounds once, as q 2^-k + delta does
+      d[i] = kScaled ? fmaf(q, inv_scale, delta[i]) : q + delta[i];
     }
   }
 
@@ -405,14 +405,17 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
   const float enc_own = reshift ? fmaf(-rho0, sig_own, s_x) : 0.f;
   SRng rng((unsigned)cell, n);
   const bool sr = L.fp16_nearest == 0;
-  // store population i (compile-time index) with post-collision deviation DSTAR
-#define STORE_POP(i, DSTAR)                                                                        \
-  do {                                                                                             \
+  // encode population i (compile-time index) with post-collision deviation
+  // DSTAR: P_ = its slot, V_ = the value to store (scaled for FP16)
+#define ENCODE_POP(i, DSTAR, P_, V_)                                                               \
+  ST *P_;                                                                                          \
+  float V_;                                                                                        \
+  {                                                                                                \
     const int cx_ = LAT::c((i), 0), cy_ = LAT::c((i), 1), cz_ = LAT::c((i), 2);                    \
     const float ds_ = (DSTAR);                                                                     \
     if (OWN_DST(i)) {                                                                              \
-      const float v_ = ds_ + enc_own;                                                              \
-      store_pop<ST>(pop + opp_of(i) * plane + cell, kScaled ? v_ * scale : v_, rng, sr);           \
+      V_ = ds_ + enc_own;                                                                          \
+      P_ = pop + opp_of(i) * plane + cell;                                                         \
     } else {                                                                                       \
       const int xm_ = xs[1 + cx_];                                                                 \
       float enc_;                                                                                  \
@@ -420,13 +423,16 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
         enc_ = -delta[opp_of(i)];                                                                  \
       else                                                                                         \
         enc_ = fmaf(-rho0, SIG_AT(cy_, cz_, xm_), s_x);                                            \
-      const float v_ = ds_ + enc_;                                                                 \
-      store_pop<ST>(pop + (i) * plane + rc.base[1 + cz_][1 + cy_] + xm_, kScaled ? v_ * scale : v_, \
-                    rng, sr);                                                                      \
+      V_ = ds_ + enc_;                                                                             \
+      P_ = pop + (i) * plane + rc.base[1 + cz_][1 + cy_] + xm_;                                    \
     }                                                                                              \
-  } while (0)
+    if (kScaled) V_ *= scale;                                                                      \
+  }
   // rest population: cu = cF = 0
-  STORE_POP(0, fmaf(om1, d[0], fmaf(omega, fmaf(M0, m15usq, dM), m3uF)));
+  {
+    ENCODE_POP(0, fmaf(om1, d[0], fmaf(omega, fmaf(M0, m15usq, dM), m3uF)), p0_, v0_);
+    store_pop<ST>(p0_, v0_, rng, sr);
+  }
   // opposite pairs (i, i+1): cu and cF change sign, so
   //   omega d^eq + Omega = A +- B,  A = omega (dM + M0 (4.5 cu^2 - 1.5 u.u)) + cf (9 cu cF - 3 u.F),
   //                                 B = 3 omega M0 cu + 3 cf cF
@@ -444,10 +450,11 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
     const float t = fmaf(M0, fmaf(4.5f * cu, cu, m15usq), dM);
     const float A = fmaf(omega, t, fmaf(cf9 * cu, cF, m3uF));
     const float B = fmaf(oM03, cu, cf3 * cF);
-    STORE_POP(i, fmaf(om1, d[i], A + B));
-    STORE_POP(i + 1, fmaf(om1, d[i + 1], A - B));
+    ENCODE_POP(i, fmaf(om1, d[i], A + B), pa_, va_);
+    ENCODE_POP(i + 1, fmaf(om1, d[i + 1], A - B), pb_, vb_);
+    store_pop_pair<ST>(pa_, va_, pb_, vb_, rng, sr);
   }
-#undef STORE_POP
+#undef ENCODE_POP
 #undef EPS_AT
 #undef DEPS_AT
 #undef SIG_AT
