@@ -262,6 +262,50 @@ def run_gpu(args, rank, world):
     return results, e2e
 
 
+def run_porous(steps=200, warmup=10, shape=(512, 256, 256), storages=("fp32", "fp16")):
+    """The porous channel: D3Q27, 512x256x256, random spheres (radius 4-12,
+    packing 0.35) smoothed by a Gaussian (sigma 3) to phi in [0.4, 1], walls
+    at y = 0 and 255, periodic x and z, tau 0.6, body force 1e-6 x, static
+    phi.  GLUPS and the fraction of the copy bandwidth at 2 Q b + 4 bytes
+    per cell (220 FP32, 112 FP16), timed with CUDA events over plain steps."""
+    import torch
+
+    from paper_2208_09267_gb300 import inputs, lbm
+    nx, ny, nz = shape
+    t0 = time.perf_counter()
+    eps = inputs.eps_random_spheres((nz, ny, nx), seed_offset=2, wall_axis=1).ravel().astype(np.float32)
+    gen_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    peak, _ = peak_hbm()
+    out = {"workload": f"D3Q27 porous channel {nx}x{ny}x{nz}, walls y, static phi (spheres r 4-12, "
+                       f"packing 0.35, Gaussian sigma 3), tau 0.6, g 1e-6 x", "steps": steps,
+           "phi_generation_s": gen_s}
+    for storage in storages:
+        lat = lbm.Lattice("D3Q27", shape, tau=0.6, storage=storage, walls=2, stream=stream.cuda_stream)
+        lat.set_epsilon(eps)
+        lat.set_force(G)
+        lat.init_equilibrium()
+        lat.step(warmup, check_every=-1)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+            a.record(stream)
+            lat.step(steps, check_every=-1)
+            b.record(stream)
+            torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        st = lat.step(1)
+        bpc = 2 * 27 * (4 if storage == "fp32" else 2) + 4
+        cells = nx * ny * nz
+        out[storage] = {"glups": cells / (ms * 1e-3) / 1e9, "ms_per_step": ms, "bytes_per_cell": bpc,
+                        "achieved_gbs": bpc * cells / (ms * 1e-3) / 1e9,
+                        "frac": bpc * cells / (ms * 1e-3) / 1e9 / peak,
+                        "kernel": "step_row_kernel" if lat.row_kernel else "step_fast_kernel",
+                        "nan_seen": bool(st["nan_seen"]), "clocks": clk.summary()}
+        lat.close()
+    return out
+
+
 def run_batched(count=64, steps=200, storages=("fp16", "fp32")):
     """Many independent lattices (half D2Q9 squares of side 32..512, half
     D3Q19 cubes of side 32..128, product-sine phi, tau in [0.55, 1.2]) advanced
@@ -388,6 +432,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-porous", action="store_true")
+    ap.add_argument("--porous-steps", type=int, default=200)
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--serve-count", type=int, default=48)
@@ -454,6 +500,8 @@ def main():
                     "traffic": profiled_traffic(st, src_hash), "clocks": rr["clocks"]}
     if rank == 0 and not args.no_batch:
         line["batched"] = run_batched(args.batch_count, args.batch_steps)
+    if rank == 0 and not args.no_porous:
+        line["porous_channel"] = run_porous(args.porous_steps)
     if rank == 0 and not args.no_serve:
         line["serving"] = run_serving(args.serve_rate, args.serve_count)
     if rank == 0 and not args.no_cpu:

@@ -110,39 +110,38 @@ cudaError_t launch_finalize(const double *partials, int nblocks, double *out, cu
   return cudaGetLastError();
 }
 
+// One block per x-row (y, z) at a time, threads along x: no index division
+// per cell, coalesced row reads (the neighbour rows come from L2).
 __global__ void shift_kernel(const float *eps, __half *sig, int nx, int nxp, int ny, int nz, unsigned qa,
                              float w0, float w1) {
-  const long long N = (long long)nxp * ny * nz;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
-       c += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(c % nxp);
-    if (x >= nx) {  // row padding: a valid value that nothing decodes
-      sig[c] = __float2half_rn(1.0f);
-      continue;
-    }
-    const long long r = c / nxp;
+  const long long rows = (long long)ny * nz;
+  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
     const int y = (int)(r % ny), z = (int)(r / ny);
-    float nb = 0.f;
-    if (qa & 1u) nb += eps[c - x + (x == nx - 1 ? 0 : x + 1)] + eps[c - x + (x == 0 ? nx - 1 : x - 1)];
-    if (qa & 2u) {
-      const long long row = (long long)z * ny;
-      nb += eps[(row + (y == ny - 1 ? 0 : y + 1)) * nxp + x] + eps[(row + (y == 0 ? ny - 1 : y - 1)) * nxp + x];
+    const long long row = r * nxp;
+    const long long ym = ((long long)z * ny + (y == 0 ? ny - 1 : y - 1)) * nxp;
+    const long long yp = ((long long)z * ny + (y == ny - 1 ? 0 : y + 1)) * nxp;
+    const long long zm = ((long long)(z == 0 ? nz - 1 : z - 1) * ny + y) * nxp;
+    const long long zp = ((long long)(z == nz - 1 ? 0 : z + 1) * ny + y) * nxp;
+    for (int x = threadIdx.x; x < nxp; x += blockDim.x) {
+      if (x >= nx) {  // row padding: a valid value that nothing decodes
+        sig[row + x] = __float2half_rn(1.0f);
+        continue;
+      }
+      float nb = 0.f;
+      if (qa & 1u) nb += eps[row + (x == nx - 1 ? 0 : x + 1)] + eps[row + (x == 0 ? nx - 1 : x - 1)];
+      if (qa & 2u) nb += eps[yp + x] + eps[ym + x];
+      if (qa & 4u) nb += eps[zp + x] + eps[zm + x];
+      sig[row + x] = __float2half_rn(fmaf(w0, eps[row + x], w1 * nb));
     }
-    if (qa & 4u) {
-      const long long pl = (long long)ny * nxp;
-      nb += eps[(long long)(z == nz - 1 ? 0 : z + 1) * pl + (long long)y * nxp + x] +
-            eps[(long long)(z == 0 ? nz - 1 : z - 1) * pl + (long long)y * nxp + x];
-    }
-    sig[c] = __float2half_rn(fmaf(w0, eps[c], w1 * nb));
   }
 }
 
 cudaError_t launch_shift(const LatticeDev &h, const float *eps, __half *sig, cudaStream_t s) {
-  const long long N = (long long)h.nxp * h.ny * h.nz;
-  long long g = (N + 255) / 256;
-  if (g > 152LL * 32) g = 152LL * 32;
-  shift_kernel<<<(int)g, 256, 0, s>>>(eps, sig, h.nx, h.nxp, h.ny, h.nz, h.quad_axes, (float)h.qw0,
-                                      (float)h.qw1);
+  const long long rows = (long long)h.ny * h.nz;
+  const int block = h.nxp >= 256 ? 256 : (h.nxp >= 128 ? 128 : 64);
+  long long g = rows < 152LL * 16 ? rows : 152LL * 16;
+  shift_kernel<<<(int)g, block, 0, s>>>(eps, sig, h.nx, h.nxp, h.ny, h.nz, h.quad_axes, (float)h.qw0,
+                                        (float)h.qw1);
   return cudaGetLastError();
 }
 

@@ -92,11 +92,12 @@ __device__ __forceinline__ void flush_member_sums(RedAcc &acc, double *sums) {
 
 // REDC: a launch of a check replay (rows may carry the check flag)
 template <class LAT, class ST, int P, bool WALLS, bool ODD, bool REDC, int NSTAGE, int MINB>
-__global__ void __launch_bounds__(kRowBlock, MINB)
+__global__ void __launch_bounds__(row_threads<MINB>(), MINB)
     batch_row_kernel(const BatchMember *__restrict__ members, const int *__restrict__ row_member,
                      const int *__restrict__ row_begin, const int2 *__restrict__ cls,
                      double *__restrict__ member_sums, int *status, int k, int kmax, int check) {
   constexpr int kStage = BatchRowCfg<LAT, ST, P>::kStage;
+  constexpr int kConsumerWarps = row_consumers<MINB>();
   __shared__ alignas(8) unsigned long long full[NSTAGE];
   __shared__ alignas(8) unsigned long long empty[NSTAGE];
   __shared__ BatchRowCtx ctx[NSTAGE];
@@ -267,7 +268,7 @@ cudaError_t launch_batch_row_t(const BatchMember *members, const int *row_member
                                int check, int grid, cudaStream_t s) {
   using C = BatchRowCfg<LAT, ST, P>;
   const int smem = C::kStage * C::kStages;
-  batch_row_kernel<LAT, ST, P, WALLS, ODD, REDC, C::kStages, C::kMinB><<<grid, kRowBlock, smem, s>>>(
+  batch_row_kernel<LAT, ST, P, WALLS, ODD, REDC, C::kStages, C::kMinB><<<grid, row_threads<C::kMinB>(), smem, s>>>(
       members, row_member, row_begin, cls, member_sums, status, k, kmax, check);
   return cudaGetLastError();
 }
@@ -295,7 +296,7 @@ int configure_batch_row_v() {
   auto *fn = batch_row_kernel<LAT, ST, P, WALLS, ODD, REDC, C::kStages, C::kMinB>;
   int occ = 0;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kRowBlock, smem) != cudaSuccess) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, row_threads<C::kMinB>(), smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }

@@ -35,10 +35,14 @@ namespace lbm {
 #ifndef LBM_ROW_CONSUMERS
 #define LBM_ROW_CONSUMERS 7
 #endif
-// consumer warps per block; + one producer warp.  With 7, two blocks give
-// every SM sub-partition four warps and 128 registers each.
-constexpr int kConsumerWarps = LBM_ROW_CONSUMERS;
-constexpr int kRowBlock = (kConsumerWarps + 1) * 32;
+// Consumer warps per block (+ one producer warp).  Two blocks per SM (MINB
+// 2) take 7: every SM sub-partition then holds four warps of up to 128
+// registers.  Where a stage is too large for two blocks per SM (MINB 1: rows
+// of 512 cells, D3Q27) one block takes 15, so the SM keeps 16 warps.
+template <int MINB>
+constexpr int row_consumers() { return MINB == 1 ? 15 : LBM_ROW_CONSUMERS; }
+template <int MINB>
+constexpr int row_threads() { return (row_consumers<MINB>() + 1) * 32; }
 constexpr unsigned kWaitSpins = 1u << 22;  // bounded mbarrier wait
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
@@ -476,7 +480,7 @@ __device__ __forceinline__ bool mbar_wait_or_abort(unsigned long long *bar, unsi
   return false;
 }
 
-// Warp-specialised row kernel.  Warp kConsumerWarps is the producer: it
+// Warp-specialised row kernel.  The last warp is the producer: it
 // stages row j into stage j % NSTAGE once the consumers have released the
 // row that used it before (empty barrier), arming the full barrier with the
 // byte count of the copies.  Each producer lane owns two of the row's copies,
@@ -485,7 +489,8 @@ __device__ __forceinline__ bool mbar_wait_or_abort(unsigned long long *bar, unsi
 // their cells and release the stage, one arrival per warp.  No block-wide
 // barrier is taken inside the loop.
 template <class LAT, class ST, bool ODD, bool RED, bool WALLS, int PITCH, int NSTAGE, int MINB>
-__global__ void __launch_bounds__(kRowBlock, MINB) step_row_kernel(const LatticeDev *__restrict__ Lp, int k) {
+__global__ void __launch_bounds__(row_threads<MINB>(), MINB) step_row_kernel(const LatticeDev *__restrict__ Lp, int k) {
+  constexpr int kConsumerWarps = row_consumers<MINB>();
   using Lay = RowLayout<LAT, ST, ODD, PITCH>;
   __shared__ LatticeDev Ls;
   __shared__ alignas(8) unsigned long long full[NSTAGE];
@@ -614,14 +619,21 @@ namespace lbm {
 #ifndef LBM_ROW_NSTAGE_256
 #define LBM_ROW_NSTAGE_256 3
 #endif
-template <int P>
-constexpr int row_stages() { return P <= 256 ? LBM_ROW_NSTAGE_256 : 2; }
+// Stages per block: 3 at two blocks per SM; with one block per SM as many as
+// fit in 216 KB, at most 6.
+template <class LAT, class ST, int P, int MINB>
+constexpr int row_stages() {
+  return MINB > 1 ? LBM_ROW_NSTAGE_256
+                  : (216 * 1024 / RowLayout<LAT, ST, true, P>::kStageBytes > 6
+                         ? 6
+                         : 216 * 1024 / RowLayout<LAT, ST, true, P>::kStageBytes);
+}
 
 template <class LAT, class ST, bool W, int P, int MINB>
 cudaError_t launch_row_v(const LatticeDev *L_dev, bool odd, int red, int k, const StepLaunch &ls,
                          cudaStream_t s) {
-  constexpr int NS = row_stages<P>();
-  const dim3 grid(ls.row_grid), block(kRowBlock);
+  constexpr int NS = row_stages<LAT, ST, P, MINB>();
+  const dim3 grid(ls.row_grid), block(row_threads<MINB>());
   if (odd) {
     const int smem = RowLayout<LAT, ST, true, P>::kStageBytes * NS;
     if (red) step_row_kernel<LAT, ST, true, true, W, P, NS, MINB><<<grid, block, smem, s>>>(L_dev, k);
@@ -648,7 +660,8 @@ cudaError_t launch_row_t(const LatticeDev *L_dev, bool odd, int red, int k, cons
 
 template <class LAT, class ST, bool W, int P, int MINB>
 int configure_row_v(int &occ) {
-  constexpr int NS = row_stages<P>();
+  constexpr int NS = row_stages<LAT, ST, P, MINB>();
+  static_assert(NS >= 2, "a row kernel needs at least two stages");
   const int smem = RowLayout<LAT, ST, true, P>::kStageBytes * NS;
   if (smem > 220 * 1024) return 0;
   cudaError_t e = cudaSuccess;
@@ -666,7 +679,7 @@ int configure_row_v(int &occ) {
                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step_row_kernel<LAT, ST, true, false, W, P, NS, MINB>,
-                                                      kRowBlock, smem);
+                                                      row_threads<MINB>(), smem);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 0;
