@@ -87,7 +87,11 @@ typedef struct {
   double tau;               /* BGK relaxation time, eq. (lbe); > 0.5 */
   double rho0;              /* reference density; p = c_s^2 (rho~ - rho0) */
   int quad_dim;             /* row of Table "weights" (1, 2, 3); 0 = number
-                               of bits in quad_axes */
+                               of bits in quad_axes; -1 = pointwise density
+                               rho~ = M0 / phi(x) (varpi_0 = 1, the other
+                               weights 0): the zeroth-moment reading of the
+                               earlier scheme that Sec. 1 says misses the
+                               pressure, for comparison only */
   unsigned quad_axes;       /* axes whose face neighbours enter eq. (quad);
                                0 = every lattice axis.  The paper picks the
                                D1Q3/D2Q5/D3Q7 rule by the number of

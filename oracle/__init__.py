@@ -117,7 +117,7 @@ def velocity_set(lattice: int):
 def quad_weights(quad_dim: int):
     w = np.zeros(2)
     if lib().oracle_quad_weights(quad_dim, w.ctypes.data):
-        raise ValueError("quad_dim must be 1, 2 or 3")
+        raise ValueError("quad_dim must be 1, 2, 3 or -1 (pointwise)")
     return w
 
 

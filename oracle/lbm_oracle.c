@@ -45,6 +45,11 @@
  *       that would enter a solid cell back to its origin in the opposite
  *       direction.  Solid cells are never updated.
  *   R7  D3Q19 (not in the paper) uses the textbook weights 1/3, 1/18, 1/36.
+ *   R8  quad_dim = -1 selects the pointwise density rho~ = M0 / phi(x)
+ *       (varpi_0 = 1, varpi_{i!=0} = 0 in eq. (quad)): the zeroth-moment
+ *       interpretation the introduction attributes to the earlier scheme of
+ *       Zhang et al., kept for the comparison of Sec. 1's claim that it
+ *       misses the pressure.  Everything else is the same update.
  *
  * Canonical evaluation order.  Every sum runs in ascending index order and
  * starts from 0.0; products are evaluated left to right as written below.
@@ -129,8 +134,10 @@ static int orc_make_vset(int lattice, orc_vset *v) {
   return 0;
 }
 
-/* Quadrature weights of Table "weights": (varpi_0, varpi_{i!=0}) for d=1,2,3. */
+/* Quadrature weights of Table "weights": (varpi_0, varpi_{i!=0}) for d=1,2,3;
+   d = -1: the pointwise phi(x) (R8). */
 static int orc_quad_weights(int quad_dim, double *w0, double *w1) {
+  if (quad_dim == -1) { *w0 = 1.0; *w1 = 0.0; return 0; }
   if (quad_dim == 1) { *w0 = 1.0 / 2.0; *w1 = 1.0 / 4.0; return 0; }
   if (quad_dim == 2) { *w0 = 1.0 / 3.0; *w1 = 1.0 / 6.0; return 0; }
   if (quad_dim == 3) { *w0 = 1.0 / 6.0; *w1 = 5.0 / 36.0; return 0; }

@@ -66,12 +66,14 @@ struct D3Q27 {
   }
 };
 
-// Quadrature weights of Table "weights" (D1Q3, D2Q5, D3Q7 rules).
+// Quadrature weights of Table "weights" (D1Q3, D2Q5, D3Q7 rules); d = -1:
+// the pointwise phi(x) (varpi_0 = 1, varpi_{i!=0} = 0), the density of the
+// earlier scheme the paper compares against (Sec. 1).
 __host__ __device__ constexpr double quad_w0(int d) {
-  return d == 1 ? 1.0 / 2.0 : (d == 2 ? 1.0 / 3.0 : 1.0 / 6.0);
+  return d == -1 ? 1.0 : (d == 1 ? 1.0 / 2.0 : (d == 2 ? 1.0 / 3.0 : 1.0 / 6.0));
 }
 __host__ __device__ constexpr double quad_w1(int d) {
-  return d == 1 ? 1.0 / 4.0 : (d == 2 ? 1.0 / 6.0 : 5.0 / 36.0);
+  return d == -1 ? 0.0 : (d == 1 ? 1.0 / 4.0 : (d == 2 ? 1.0 / 6.0 : 5.0 / 36.0));
 }
 
 }  // namespace lbm

@@ -114,7 +114,7 @@ static int validate_params(const lbm_vanse_params *p, std::string &why) {
   const unsigned qa = p->quad_axes ? p->quad_axes : axes_mask;
   const int nbits = __builtin_popcount(qa);
   const int qd = p->quad_dim ? p->quad_dim : nbits;
-  if (qd < 1 || qd > 3) { why = "quad_dim must be 1, 2 or 3"; return 0; }
+  if (qd != -1 && (qd < 1 || qd > 3)) { why = "quad_dim must be 1, 2, 3 or -1 (pointwise)"; return 0; }
   for (int a = 0; a < 3; ++a) {
     const int n = a == 0 ? p->nx : (a == 1 ? p->ny : p->nz);
     if ((p->walls >> a) & 1u) {

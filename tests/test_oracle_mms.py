@@ -34,12 +34,12 @@ def _golden_eoc():
     raise AssertionError("eoc missing from golden file")
 
 
-def run_mms(example, N, t_end, lattice=None, chunk=4000):
+def run_mms(example, N, t_end, lattice=None, chunk=4000, quad_dim=None):
     m = I.MMS(example, N)
     lat = lattice or m.lattice
     f0 = m.lattice_fields(0)
     nz, ny, nx = m.shape
-    P = oracle.Problem(lat, nx, ny, nz, tau=m.tau, quad_axes=m.quad_axes)
+    P = oracle.Problem(lat, nx, ny, nz, tau=m.tau, quad_axes=m.quad_axes, quad_dim=quad_dim)
     P.set_epsilon(f0["eps"])
     P.set_force((0, 0, 0), f0["force"])
     f = P.init(p0=f0["p"], u0=f0["u"], half_force=True, with_integral=True)
@@ -125,3 +125,36 @@ def test_stationary_2d_example_on_3d_lattices(lattice):
     for name, e in (("u", _eoc(eu1, eu2)), ("p", _eoc(ep1, ep2))):
         for norm in ("L1", "L2"):
             assert abs(e[norm] - target) < EOC_TOL, (name, norm, e[norm])
+
+
+def test_pointwise_density_is_m0_over_phi():
+    """quad_dim = -1: rho~ = M0 / phi(x) exactly (varpi_0 = 1, the other
+    quadrature weights 0), on a random state and a varying phi."""
+    g = np.random.default_rng(31)
+    P = oracle.Problem("D2Q9", 12, 10, 1, tau=0.7, quad_dim=-1,
+                       eps_ref=0.5 + 0.4 * g.random((1, 10, 12)))
+    f = P.init()
+    f = P.run(f, 0, 3)
+    mo = P.moments(f, 3)
+    phi = P.eps_ref.reshape(P.shape)
+    assert np.array_equal(mo["rho"], mo["M0"] / phi)
+    Pc = oracle.Problem("D2Q9", 12, 10, 1, tau=0.7, eps_ref=P.eps_ref.reshape(P.shape))
+    assert not np.array_equal(Pc.moments(f, 3)["rho"], mo["rho"])
+
+
+def test_pointwise_density_misses_the_pressure():
+    """Sec. 1: a scheme whose zeroth moment is read as rho phi(x) (the
+    pointwise density) recovers the velocity but not the pressure.  On
+    Example 1 (N = 16 -> 32) the velocity still converges at second order
+    while the pressure error stays O(1) and does not converge; the
+    consistent density (eq. (density) with eq. (quad)) gives order 2 for
+    both (the tests above)."""
+    target = _golden_eoc()
+    eu1, ep1 = run_mms(1, 16, 15.0, quad_dim=-1)
+    eu2, ep2 = run_mms(1, 32, 15.0, quad_dim=-1)
+    for norm, v in _eoc(eu1, eu2).items():
+        assert abs(v - target) < EOC_TOL, ("u", norm, v)
+    for norm, v in _eoc(ep1, ep2).items():
+        assert abs(v) < 0.5, ("p", norm, v)
+    _, epc = run_mms(1, 32, 15.0)
+    assert ep2["L2"] > 100 * epc["L2"]
