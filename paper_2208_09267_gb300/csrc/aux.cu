@@ -57,10 +57,13 @@ cudaError_t launch_step(const LatticeDev &h, const LatticeDev *L_dev, long long 
   const bool odd = ((n_host + k) & 1) != 0;
   if (h.storage == 0) return launch_step_exact(h.lattice, L_dev, odd, red, k, ls, s);
   if (ls.row) {
+    // bit 1: this step decodes with the previous phi's shift (set_epsilon
+    // since the last step); the row kernel is instantiated for both cases
+    const int rr = (red ? 1 : 0) | (h.sig_rd != h.sig_wr ? 2 : 0);
     switch (h.lattice) {
-      case 0: return launch_step_row_d2q9(L_dev, h.storage, odd, red, k, ls, s);
-      case 1: return launch_step_row_d3q19(L_dev, h.storage, odd, red, k, ls, s);
-      case 2: return launch_step_row_d3q27(L_dev, h.storage, odd, red, k, ls, s);
+      case 0: return launch_step_row_d2q9(L_dev, h.storage, odd, rr, k, ls, s);
+      case 1: return launch_step_row_d3q19(L_dev, h.storage, odd, rr, k, ls, s);
+      case 2: return launch_step_row_d3q27(L_dev, h.storage, odd, rr, k, ls, s);
     }
     return cudaErrorInvalidValue;
   }

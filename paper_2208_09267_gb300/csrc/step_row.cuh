@@ -246,7 +246,10 @@ __device__ __forceinline__ void issue_copy(const RowCopy &c, unsigned char *stag
 
 // Update the 32-cell chunk [x0, x0 + 32) of one staged row (one cell per
 // lane).
-template <class LAT, class ST, bool ODD, bool RED, bool WALLS, int PITCH>
+// RS: the step after a phi refresh decodes with the old shift and encodes
+// with the new one ("reshift").  0: no refresh pending, 1: pending (both
+// known at launch), 2: read it from the descriptor.
+template <class LAT, class ST, bool ODD, bool RED, bool WALLS, int PITCH, int RS = 2>
 __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsigned char *stage,
                                                  const RowCtx &rc, long long n, float dn, float dn_force,
                                                  int x, RedAcc &acc) {
@@ -262,7 +265,8 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
   const float rho0 = L.rho0f;
   const float inv_scale = L.inv_scale, scale = L.scale;
   const __half *__restrict__ srd = L.sig_rd;
-  const bool reshift = srd != L.sig_wr;  // shift changed by the last set_epsilon
+  // shift changed by the last set_epsilon
+  const bool reshift = RS == 2 ? srd != L.sig_wr : RS == 1;
   ST *__restrict__ pop = static_cast<ST *>(L.pop);
   const int plane = (int)L.plane;
   const float omega = L.omegaf;
@@ -488,7 +492,7 @@ __device__ __forceinline__ bool mbar_wait_or_abort(unsigned long long *bar, unsi
 // besides the copies.  The consumer warps wait on the full barrier, update
 // their cells and release the stage, one arrival per warp.  No block-wide
 // barrier is taken inside the loop.
-template <class LAT, class ST, bool ODD, bool RED, bool WALLS, int PITCH, int NSTAGE, int MINB>
+template <class LAT, class ST, bool ODD, bool RED, bool WALLS, int PITCH, int NSTAGE, int MINB, int RS>
 __global__ void __launch_bounds__(row_threads<MINB>(), MINB) step_row_kernel(const LatticeDev *__restrict__ Lp, int k) {
   constexpr int kConsumerWarps = row_consumers<MINB>();
   using Lay = RowLayout<LAT, ST, ODD, PITCH>;
@@ -599,7 +603,7 @@ __global__ void __launch_bounds__(row_threads<MINB>(), MINB) step_row_kernel(con
       const int nchunks = (L.nx + 31) >> 5;
       const int first = (warp - (int)(((long long)j * nchunks) % kConsumerWarps) + kConsumerWarps) % kConsumerWarps;
       for (int c = first; c < nchunks; c += kConsumerWarps)
-        update_row_chunk<LAT, ST, ODD, RED, WALLS, PITCH>(L, stages + s * Lay::kStageBytes, ctx[s], n, dn,
+        update_row_chunk<LAT, ST, ODD, RED, WALLS, PITCH, RS>(L, stages + s * Lay::kStageBytes, ctx[s], n, dn,
                                                           dn_force, (c << 5) + lane, acc);
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[s]);
@@ -629,21 +633,30 @@ constexpr int row_stages() {
                          : 216 * 1024 / RowLayout<LAT, ST, true, P>::kStageBytes);
 }
 
-template <class LAT, class ST, bool W, int P, int MINB>
-cudaError_t launch_row_v(const LatticeDev *L_dev, bool odd, int red, int k, const StepLaunch &ls,
-                         cudaStream_t s) {
+template <class LAT, class ST, bool W, int P, int MINB, int RS>
+cudaError_t launch_row_rs(const LatticeDev *L_dev, bool odd, bool red, int k, const StepLaunch &ls,
+                          cudaStream_t s) {
   constexpr int NS = row_stages<LAT, ST, P, MINB>();
   const dim3 grid(ls.row_grid), block(row_threads<MINB>());
   if (odd) {
     const int smem = RowLayout<LAT, ST, true, P>::kStageBytes * NS;
-    if (red) step_row_kernel<LAT, ST, true, true, W, P, NS, MINB><<<grid, block, smem, s>>>(L_dev, k);
-    else step_row_kernel<LAT, ST, true, false, W, P, NS, MINB><<<grid, block, smem, s>>>(L_dev, k);
+    if (red) step_row_kernel<LAT, ST, true, true, W, P, NS, MINB, RS><<<grid, block, smem, s>>>(L_dev, k);
+    else step_row_kernel<LAT, ST, true, false, W, P, NS, MINB, RS><<<grid, block, smem, s>>>(L_dev, k);
   } else {
     const int smem = RowLayout<LAT, ST, false, P>::kStageBytes * NS;
-    if (red) step_row_kernel<LAT, ST, false, true, W, P, NS, MINB><<<grid, block, smem, s>>>(L_dev, k);
-    else step_row_kernel<LAT, ST, false, false, W, P, NS, MINB><<<grid, block, smem, s>>>(L_dev, k);
+    if (red) step_row_kernel<LAT, ST, false, true, W, P, NS, MINB, RS><<<grid, block, smem, s>>>(L_dev, k);
+    else step_row_kernel<LAT, ST, false, false, W, P, NS, MINB, RS><<<grid, block, smem, s>>>(L_dev, k);
   }
   return cudaGetLastError();
+}
+
+// red: bit 0 a check step, bit 1 the step decodes with the shift of the
+// previous phi (the first step after a refresh)
+template <class LAT, class ST, bool W, int P, int MINB>
+cudaError_t launch_row_v(const LatticeDev *L_dev, bool odd, int red, int k, const StepLaunch &ls,
+                         cudaStream_t s) {
+  if (red & 2) return launch_row_rs<LAT, ST, W, P, MINB, 1>(L_dev, odd, (red & 1) != 0, k, ls, s);
+  return launch_row_rs<LAT, ST, W, P, MINB, 0>(L_dev, odd, (red & 1) != 0, k, ls, s);
 }
 
 template <class LAT, class ST, int MINB>
@@ -658,6 +671,13 @@ cudaError_t launch_row_t(const LatticeDev *L_dev, bool odd, int red, int k, cons
   return launch_row_v<LAT, ST, false, 256, MINB>(L_dev, odd, red, k, ls, s);
 }
 
+template <class LAT, class ST, bool W, int P, int MINB, bool ODD, bool RED, int RS>
+cudaError_t configure_row_one(int smem) {
+  constexpr int NS = row_stages<LAT, ST, P, MINB>();
+  return cudaFuncSetAttribute(step_row_kernel<LAT, ST, ODD, RED, W, P, NS, MINB, RS>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
 template <class LAT, class ST, bool W, int P, int MINB>
 int configure_row_v(int &occ) {
   constexpr int NS = row_stages<LAT, ST, P, MINB>();
@@ -665,21 +685,20 @@ int configure_row_v(int &occ) {
   const int smem = RowLayout<LAT, ST, true, P>::kStageBytes * NS;
   if (smem > 220 * 1024) return 0;
   cudaError_t e = cudaSuccess;
+#define LBM_CFG(ODD, RED, RS) \
+  if (e == cudaSuccess) e = configure_row_one<LAT, ST, W, P, MINB, ODD, RED, RS>(smem)
+  LBM_CFG(true, false, 0);
+  LBM_CFG(true, true, 0);
+  LBM_CFG(false, false, 0);
+  LBM_CFG(false, true, 0);
+  LBM_CFG(true, false, 1);
+  LBM_CFG(true, true, 1);
+  LBM_CFG(false, false, 1);
+  LBM_CFG(false, true, 1);
+#undef LBM_CFG
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(step_row_kernel<LAT, ST, true, false, W, P, NS, MINB>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(step_row_kernel<LAT, ST, true, true, W, P, NS, MINB>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(step_row_kernel<LAT, ST, false, false, W, P, NS, MINB>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(step_row_kernel<LAT, ST, false, true, W, P, NS, MINB>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step_row_kernel<LAT, ST, true, false, W, P, NS, MINB>,
-                                                      row_threads<MINB>(), smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &occ, step_row_kernel<LAT, ST, true, false, W, P, NS, MINB, 0>, row_threads<MINB>(), smem);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 0;
