@@ -36,18 +36,20 @@ int handle_push(lbm_vanse_t h);
 cudaStream_t handle_stream(lbm_vanse_t h);
 void set_global_error(const char *msg);
 int sm_count();
-// batched row kernel, one entry per lattice type (batch_row_*.cu); the
-// shape class selects the row pitch 64, 128, 256 or 512 (bits 0-1) and
-// walls on y/z (bit 2)
-cudaError_t launch_batch_row_d2q9(int, int, int, int, const BatchMember *, const int *, const int *, const int2 *, double *,
-                                  int *, int, int, int, int, cudaStream_t);
-cudaError_t launch_batch_row_d3q19(int, int, int, int, const BatchMember *, const int *, const int *, const int2 *, double *,
-                                   int *, int, int, int, int, cudaStream_t);
-cudaError_t launch_batch_row_d3q27(int, int, int, int, const BatchMember *, const int *, const int *, const int2 *, double *,
-                                   int *, int, int, int, int, cudaStream_t);
-int configure_batch_row_d2q9(int storage, int pclass);
-int configure_batch_row_d3q19(int storage, int pclass);
-int configure_batch_row_d3q27(int storage, int pclass);
+// batched row kernel, one entry per lattice type and storage
+// (batch_row_*_f32.cu, batch_row_*_f16.cu); the shape class selects the row
+// pitch 64, 128, 256 or 512 (bits 0-1) and walls on y/z (bit 2)
+#define LBM_BR_DECL(NAME)                                                                                   \
+  cudaError_t launch_batch_row_##NAME(int, int, int, int, const BatchMember *, const int *, const int *,     \
+                                      const int2 *, double *, int *, int, int, int, int, cudaStream_t);      \
+  int configure_batch_row_##NAME(int shape);
+LBM_BR_DECL(d2q9_f32)
+LBM_BR_DECL(d2q9_f16)
+LBM_BR_DECL(d3q19_f32)
+LBM_BR_DECL(d3q19_f16)
+LBM_BR_DECL(d3q27_f32)
+LBM_BR_DECL(d3q27_f16)
+#undef LBM_BR_DECL
 }  // namespace lbm
 
 using namespace lbm;
@@ -95,11 +97,11 @@ __global__ void __launch_bounds__(kBatchBlock) batch_step_kernel(const BatchMemb
       const int y = r % ny;
       const int z = r / ny;
       if (red_here) {
-        if (n & 1) update_cell_fast<LAT, ST, true, true>(L, n, x, y, z, acc);
-        else update_cell_fast<LAT, ST, false, true>(L, n, x, y, z, acc);
+        if (n & 1) update_cell_fast<LAT, ST, true, true>(L, n, x, y, z, acc, k == 0);
+        else update_cell_fast<LAT, ST, false, true>(L, n, x, y, z, acc, k == 0);
       } else {
-        if (n & 1) update_cell_fast<LAT, ST, true, false>(L, n, x, y, z, acc);
-        else update_cell_fast<LAT, ST, false, false>(L, n, x, y, z, acc);
+        if (n & 1) update_cell_fast<LAT, ST, true, false>(L, n, x, y, z, acc, k == 0);
+        else update_cell_fast<LAT, ST, false, false>(L, n, x, y, z, acc, k == 0);
       }
     }
     if (red_here) {
@@ -143,27 +145,33 @@ cudaError_t launch_row_class(int cls, int odd, const BatchMember *members, const
                              const int *row_begin, const int2 *cls_dev, double *member_sums, int *status, int k,
                              int kmax, int red, int grid, cudaStream_t s) {
   const int type = cls / kPitchClasses, pclass = cls % kPitchClasses;
-  const int lattice = type / 2, storage = (type & 1) ? 2 : 1;
-  switch (lattice) {
-    case 0: return launch_batch_row_d2q9(storage, pclass, odd, red, members, row_member, row_begin, cls_dev, member_sums,
-                                         status, k, kmax, red, grid, s);
-    case 1: return launch_batch_row_d3q19(storage, pclass, odd, red, members, row_member, row_begin, cls_dev, member_sums,
-                                          status, k, kmax, red, grid, s);
-    case 2: return launch_batch_row_d3q27(storage, pclass, odd, red, members, row_member, row_begin, cls_dev, member_sums,
-                                          status, k, kmax, red, grid, s);
+  const int first = k == 0;
+#define LBM_BR_CALL(NAME) \
+  return launch_batch_row_##NAME(pclass, odd, red, first, members, row_member, row_begin, cls_dev, member_sums, \
+                                 status, k, kmax, red, grid, s)
+  switch (type) {
+    case 0: LBM_BR_CALL(d2q9_f32);
+    case 1: LBM_BR_CALL(d2q9_f16);
+    case 2: LBM_BR_CALL(d3q19_f32);
+    case 3: LBM_BR_CALL(d3q19_f16);
+    case 4: LBM_BR_CALL(d3q27_f32);
+    case 5: LBM_BR_CALL(d3q27_f16);
   }
+#undef LBM_BR_CALL
   return cudaErrorInvalidValue;
 }
 
 // Resident blocks x SMs of a row class; 0 when it cannot run.
 int row_class_grid(int cls) {
   const int type = cls / kPitchClasses, pclass = cls % kPitchClasses;
-  const int lattice = type / 2, storage = (type & 1) ? 2 : 1;
   int occ = 0;
-  switch (lattice) {
-    case 0: occ = configure_batch_row_d2q9(storage, pclass); break;
-    case 1: occ = configure_batch_row_d3q19(storage, pclass); break;
-    case 2: occ = configure_batch_row_d3q27(storage, pclass); break;
+  switch (type) {
+    case 0: occ = configure_batch_row_d2q9_f32(pclass); break;
+    case 1: occ = configure_batch_row_d2q9_f16(pclass); break;
+    case 2: occ = configure_batch_row_d3q19_f32(pclass); break;
+    case 3: occ = configure_batch_row_d3q19_f16(pclass); break;
+    case 4: occ = configure_batch_row_d3q27_f32(pclass); break;
+    case 5: occ = configure_batch_row_d3q27_f16(pclass); break;
   }
   return occ > 0 ? occ * sm_count() : 0;
 }

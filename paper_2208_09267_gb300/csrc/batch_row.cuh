@@ -90,8 +90,12 @@ __device__ __forceinline__ void flush_member_sums(RedAcc &acc, double *sums) {
   }
 }
 
-// REDC: a launch of a check replay (rows may carry the check flag)
-template <class LAT, class ST, int P, bool WALLS, bool ODD, bool REDC, int NSTAGE, int MINB>
+// REDC: a launch of a check replay (rows may carry the check flag).  RS 2:
+// the first step of a replay, where a member's phi refresh since its last
+// step is still pending (its descriptor tells); RS 0: later steps (the
+// descriptors' shifts are committed only after the replay, so they must not
+// be read as pending there).
+template <class LAT, class ST, int P, bool WALLS, bool ODD, bool REDC, int RS, int NSTAGE, int MINB>
 __global__ void __launch_bounds__(row_threads<MINB>(), MINB)
     batch_row_kernel(const BatchMember *__restrict__ members, const int *__restrict__ row_member,
                      const int *__restrict__ row_begin, const int2 *__restrict__ cls,
@@ -249,8 +253,8 @@ __global__ void __launch_bounds__(row_threads<MINB>(), MINB)
         const int first = (warp - chunk + kConsumerWarps) % kConsumerWarps;
         for (int c = first; c < nchunks; c += kConsumerWarps) {
           const int x = (c << 5) + lane;
-          if (red) update_row_chunk<LAT, ST, ODD, REDC, WALLS, P>(Lm, data, ctx[s].rc, n, dn, dn_force, x, acc);
-          else update_row_chunk<LAT, ST, ODD, false, WALLS, P>(Lm, data, ctx[s].rc, n, dn, dn_force, x, acc);
+          if (red) update_row_chunk<LAT, ST, ODD, REDC, WALLS, P, RS>(Lm, data, ctx[s].rc, n, dn, dn_force, x, acc);
+          else update_row_chunk<LAT, ST, ODD, false, WALLS, P, RS>(Lm, data, ctx[s].rc, n, dn, dn_force, x, acc);
         }
         chunk = (chunk + nchunks) % kConsumerWarps;
       }
@@ -262,38 +266,51 @@ __global__ void __launch_bounds__(row_threads<MINB>(), MINB)
 }
 
 // Host side: launch of one class part.
-template <class LAT, class ST, int P, bool WALLS, bool ODD, bool REDC>
+template <class LAT, class ST, int P, bool WALLS, bool ODD, bool REDC, int RS>
 cudaError_t launch_batch_row_t(const BatchMember *members, const int *row_member, const int *row_begin,
                                const int2 *cls, double *member_sums, int *status, int k, int kmax,
                                int check, int grid, cudaStream_t s) {
   using C = BatchRowCfg<LAT, ST, P>;
   const int smem = C::kStage * C::kStages;
-  batch_row_kernel<LAT, ST, P, WALLS, ODD, REDC, C::kStages, C::kMinB><<<grid, row_threads<C::kMinB>(), smem, s>>>(
+  batch_row_kernel<LAT, ST, P, WALLS, ODD, REDC, RS, C::kStages, C::kMinB><<<grid, row_threads<C::kMinB>(), smem, s>>>(
       members, row_member, row_begin, cls, member_sums, status, k, kmax, check);
   return cudaGetLastError();
 }
 
-template <class LAT, class ST, int P, bool WALLS>
-cudaError_t launch_batch_row_t(bool odd, bool redc, const BatchMember *members, const int *row_member,
-                               const int *row_begin, const int2 *cls, double *member_sums, int *status, int k,
-                               int kmax, int check, int grid, cudaStream_t s) {
-  if (odd) {
-    if (redc) return launch_batch_row_t<LAT, ST, P, WALLS, true, true>(members, row_member, row_begin, cls,
-                                                                        member_sums, status, k, kmax, check, grid, s);
-    return launch_batch_row_t<LAT, ST, P, WALLS, true, false>(members, row_member, row_begin, cls, member_sums,
+template <class LAT, class ST, int P, bool WALLS, bool ODD, bool REDC>
+cudaError_t launch_batch_row_rs(bool first, const BatchMember *members, const int *row_member,
+                                const int *row_begin, const int2 *cls, double *member_sums, int *status, int k,
+                                int kmax, int check, int grid, cudaStream_t s) {
+  if (first)
+    return launch_batch_row_t<LAT, ST, P, WALLS, ODD, REDC, 2>(members, row_member, row_begin, cls, member_sums,
                                                                status, k, kmax, check, grid, s);
-  }
-  if (redc) return launch_batch_row_t<LAT, ST, P, WALLS, false, true>(members, row_member, row_begin, cls,
-                                                                       member_sums, status, k, kmax, check, grid, s);
-  return launch_batch_row_t<LAT, ST, P, WALLS, false, false>(members, row_member, row_begin, cls, member_sums,
-                                                              status, k, kmax, check, grid, s);
+  return launch_batch_row_t<LAT, ST, P, WALLS, ODD, REDC, 0>(members, row_member, row_begin, cls, member_sums,
+                                                             status, k, kmax, check, grid, s);
 }
 
-template <class LAT, class ST, int P, bool WALLS, bool ODD, bool REDC>
+// first: the first step of the replay (k == 0)
+template <class LAT, class ST, int P, bool WALLS>
+cudaError_t launch_batch_row_t(bool odd, bool redc, bool first, const BatchMember *members,
+                               const int *row_member, const int *row_begin, const int2 *cls,
+                               double *member_sums, int *status, int k, int kmax, int check, int grid,
+                               cudaStream_t s) {
+  if (odd) {
+    if (redc) return launch_batch_row_rs<LAT, ST, P, WALLS, true, true>(first, members, row_member, row_begin, cls,
+                                                                         member_sums, status, k, kmax, check, grid, s);
+    return launch_batch_row_rs<LAT, ST, P, WALLS, true, false>(first, members, row_member, row_begin, cls,
+                                                                member_sums, status, k, kmax, check, grid, s);
+  }
+  if (redc) return launch_batch_row_rs<LAT, ST, P, WALLS, false, true>(first, members, row_member, row_begin, cls,
+                                                                        member_sums, status, k, kmax, check, grid, s);
+  return launch_batch_row_rs<LAT, ST, P, WALLS, false, false>(first, members, row_member, row_begin, cls,
+                                                               member_sums, status, k, kmax, check, grid, s);
+}
+
+template <class LAT, class ST, int P, bool WALLS, bool ODD, bool REDC, int RS>
 int configure_batch_row_v() {
   using C = BatchRowCfg<LAT, ST, P>;
   const int smem = C::kStage * C::kStages;
-  auto *fn = batch_row_kernel<LAT, ST, P, WALLS, ODD, REDC, C::kStages, C::kMinB>;
+  auto *fn = batch_row_kernel<LAT, ST, P, WALLS, ODD, REDC, RS, C::kStages, C::kMinB>;
   int occ = 0;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, row_threads<C::kMinB>(), smem) != cudaSuccess) {
@@ -303,18 +320,22 @@ int configure_batch_row_v() {
   return occ;
 }
 
-// Resident blocks per SM of a class: the least over its four instantiations
+// Resident blocks per SM of a class: the least over its instantiations
 // (after the shared-memory opt-in); 0 on failure.
 template <class LAT, class ST, int P, bool WALLS>
 int configure_batch_row_t() {
   static_assert(BatchRowCfg<LAT, ST, P>::kStages >= 2, "a class needs at least two stages");
-  int occ = configure_batch_row_v<LAT, ST, P, WALLS, false, false>();
-  int o = configure_batch_row_v<LAT, ST, P, WALLS, true, false>();
-  occ = o < occ ? o : occ;
-  o = configure_batch_row_v<LAT, ST, P, WALLS, false, true>();
-  occ = o < occ ? o : occ;
-  o = configure_batch_row_v<LAT, ST, P, WALLS, true, true>();
-  return o < occ ? o : occ;
+  const int o[8] = {configure_batch_row_v<LAT, ST, P, WALLS, false, false, 0>(),
+                    configure_batch_row_v<LAT, ST, P, WALLS, true, false, 0>(),
+                    configure_batch_row_v<LAT, ST, P, WALLS, false, true, 0>(),
+                    configure_batch_row_v<LAT, ST, P, WALLS, true, true, 0>(),
+                    configure_batch_row_v<LAT, ST, P, WALLS, false, false, 2>(),
+                    configure_batch_row_v<LAT, ST, P, WALLS, true, false, 2>(),
+                    configure_batch_row_v<LAT, ST, P, WALLS, false, true, 2>(),
+                    configure_batch_row_v<LAT, ST, P, WALLS, true, true, 2>()};
+  int occ = o[0];
+  for (int i = 1; i < 8; ++i) occ = o[i] < occ ? o[i] : occ;
+  return occ;
 }
 
 }  // namespace lbm

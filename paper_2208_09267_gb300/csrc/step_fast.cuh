@@ -169,9 +169,12 @@ struct RedAcc {
   double v[kRedWidth];
 };
 
+// first: this step is the first since the descriptor's shifts were last
+// committed (a pending refresh applies to it only); the batched kernels,
+// which commit after a replay of several steps, pass false after the first.
 template <class LAT, class ST, bool ODD, bool RED>
 __device__ __forceinline__ void update_cell_fast(const LatticeDev &L, long long n, int x, int y,
-                                                 int z, RedAcc &acc) {
+                                                 int z, RedAcc &acc, bool first = true) {
   constexpr int Q = LAT::Q;
   constexpr int D = LAT::D;
   const int nx = L.nx, ny = L.ny, nz = L.nz;
@@ -182,8 +185,8 @@ __device__ __forceinline__ void update_cell_fast(const LatticeDev &L, long long 
   const long long cell = C.at(0, 0, 0);
   const long long plane = L.plane;
   ST *__restrict__ pop = static_cast<ST *>(L.pop);
-  const __half *__restrict__ srd = L.sig_rd;
   const __half *__restrict__ swr = L.sig_wr;
+  const __half *__restrict__ srd = first ? L.sig_rd : swr;
   const float rho0 = L.rho0f;
   const float inv_scale = L.inv_scale, scale = L.scale;
   const float s_x = rho0 * __half2float(srd[cell]);
