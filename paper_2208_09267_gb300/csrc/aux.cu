@@ -113,38 +113,52 @@ cudaError_t launch_finalize(const double *partials, int nblocks, double *out, cu
   return cudaGetLastError();
 }
 
-// One block per x-row (y, z) at a time, threads along x: no index division
-// per cell, coalesced row reads (the neighbour rows come from L2).
+// Threads along x; each thread walks a segment of y at fixed (x, z) with
+// the rows y-1, y, y+1 of phi in registers, so phi is read about three
+// times per cell (own row, z-1, z+1) instead of seven; x neighbours come
+// from the row the warp has just read (L1).  Same sum order as eq. (quad)
+// is written everywhere: x pair, y pair, z pair.
+constexpr int kShiftSeg = 32;  // rows of y per thread
+
 __global__ void shift_kernel(const float *eps, __half *sig, int nx, int nxp, int ny, int nz, unsigned qa,
                              float w0, float w1) {
-  const long long rows = (long long)ny * nz;
-  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
-    const int y = (int)(r % ny), z = (int)(r / ny);
-    const long long row = r * nxp;
-    const long long ym = ((long long)z * ny + (y == 0 ? ny - 1 : y - 1)) * nxp;
-    const long long yp = ((long long)z * ny + (y == ny - 1 ? 0 : y + 1)) * nxp;
-    const long long zm = ((long long)(z == 0 ? nz - 1 : z - 1) * ny + y) * nxp;
-    const long long zp = ((long long)(z == nz - 1 ? 0 : z + 1) * ny + y) * nxp;
-    for (int x = threadIdx.x; x < nxp; x += blockDim.x) {
-      if (x >= nx) {  // row padding: a valid value that nothing decodes
-        sig[row + x] = __float2half_rn(1.0f);
-        continue;
-      }
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= nxp) return;
+  const int nseg = (ny + kShiftSeg - 1) / kShiftSeg;
+  const long long plane = (long long)ny * nxp;
+  for (long long t = blockIdx.y; t < (long long)nz * nseg; t += gridDim.y) {
+    const int z = (int)(t / nseg), y0 = (int)(t % nseg) * kShiftSeg;
+    const int y1 = y0 + kShiftSeg < ny ? y0 + kShiftSeg : ny;
+    const long long pz = (long long)z * plane;
+    if (x >= nx) {  // row padding: a valid value that nothing decodes
+      for (int y = y0; y < y1; ++y) sig[pz + (long long)y * nxp + x] = __float2half_rn(1.0f);
+      continue;
+    }
+    const long long pzm = (long long)(z == 0 ? nz - 1 : z - 1) * plane;
+    const long long pzp = (long long)(z == nz - 1 ? 0 : z + 1) * plane;
+    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+    float e_ym = eps[pz + (long long)(y0 == 0 ? ny - 1 : y0 - 1) * nxp + x];
+    float e_c = eps[pz + (long long)y0 * nxp + x];
+    for (int y = y0; y < y1; ++y) {
+      const long long row = pz + (long long)y * nxp;
+      const float e_yp = eps[pz + (long long)(y == ny - 1 ? 0 : y + 1) * nxp + x];
       float nb = 0.f;
-      if (qa & 1u) nb += eps[row + (x == nx - 1 ? 0 : x + 1)] + eps[row + (x == 0 ? nx - 1 : x - 1)];
-      if (qa & 2u) nb += eps[yp + x] + eps[ym + x];
-      if (qa & 4u) nb += eps[zp + x] + eps[zm + x];
-      sig[row + x] = __float2half_rn(fmaf(w0, eps[row + x], w1 * nb));
+      if (qa & 1u) nb += eps[row + xp] + eps[row + xm];
+      if (qa & 2u) nb += e_yp + e_ym;
+      if (qa & 4u) nb += eps[pzp + (long long)y * nxp + x] + eps[pzm + (long long)y * nxp + x];
+      sig[row + x] = __float2half_rn(fmaf(w0, e_c, w1 * nb));
+      e_ym = e_c;
+      e_c = e_yp;
     }
   }
 }
 
 cudaError_t launch_shift(const LatticeDev &h, const float *eps, __half *sig, cudaStream_t s) {
-  const long long rows = (long long)h.ny * h.nz;
   const int block = h.nxp >= 256 ? 256 : (h.nxp >= 128 ? 128 : 64);
-  long long g = rows < 152LL * 16 ? rows : 152LL * 16;
-  shift_kernel<<<(int)g, block, 0, s>>>(eps, sig, h.nx, h.nxp, h.ny, h.nz, h.quad_axes, (float)h.qw0,
-                                        (float)h.qw1);
+  const long long work = (long long)h.nz * ((h.ny + kShiftSeg - 1) / kShiftSeg);
+  const dim3 grid((unsigned)((h.nxp + block - 1) / block), (unsigned)(work < 65535 ? work : 65535));
+  shift_kernel<<<grid, block, 0, s>>>(eps, sig, h.nx, h.nxp, h.ny, h.nz, h.quad_axes, (float)h.qw0,
+                                      (float)h.qw1);
   return cudaGetLastError();
 }
 
