@@ -230,34 +230,66 @@ def run_gpu(args, rank, world):
                             "kernel": f"{kname}<D3Q19,{'float' if storage == 'fp32' else '__half'}>"}
         lat.close()
 
-    # end to end through the C ABI with host buffers (FP32)
+    # end to end through the C ABI with host buffers (FP32).  The refreshes
+    # reach the library the way a streaming application would hand them
+    # over: a producer thread copies each refresh's phi_ref and d_t phi into
+    # a ring of three pinned staging buffers, ahead of use; the main loop
+    # steps and passes the staged host buffers to set_epsilon (H2D copy and
+    # checks inside the call).  A fresh pinned buffer per refresh would
+    # instead pay the host-memory first-touch of the device's DMA (measured
+    # ~8 GB/s against ~170 GB/s once warm).
     e2e = None
     if not args.no_e2e:
+        import queue
+        ring = 3
+        st_e = torch.empty((ring, N), dtype=torch.float32, pin_memory=True)
+        st_d = torch.empty((ring, N), dtype=torch.float32, pin_memory=True)
+        st_e_np = [st_e[i].numpy() for i in range(ring)]
+        st_d_np = [st_d[i].numpy() for i in range(ring)]
+        free = threading.Semaphore(ring)
+        ready = queue.Queue()
+
+        def producer(first, count):
+            for q in range(count):
+                free.acquire()
+                slot = (first + q) % ring
+                np.copyto(st_e_np[slot], host_e[first + q].numpy())
+                np.copyto(st_d_np[slot], host_d[first + q].numpy())
+                ready.put(slot)
+
         lat = lbm.Lattice("D3Q19", (L, L, L), tau=TAU, storage=args.storages[0],
                           stream=stream.cuda_stream, block=tuple(args.block))
         lat.set_force(G)
-        he = [host_e[j].numpy() for j in range(nref)]
-        hd = [host_d[j].numpy() for j in range(nref)]
-        lat.set_epsilon(he[0], hd[0], 0)
+        nwarm = args.warmup // K_EPS
+        chunks = max(1, args.steps // K_EPS)
+        prod = threading.Thread(target=producer, args=(0, min(nref, nwarm + chunks + 1)), daemon=True)
+        prod.start()
+        slot = ready.get()
+        lat.set_epsilon(st_e_np[slot], st_d_np[slot], 0)
+        free.release()
         lat.init_equilibrium()
-        for j in range(args.warmup // K_EPS):
+        for j in range(nwarm):
             lat.step(K_EPS)
-            lat.set_epsilon(he[j + 1], hd[j + 1], (j + 1) * K_EPS)
+            slot = ready.get()
+            lat.set_epsilon(st_e_np[slot], st_d_np[slot], (j + 1) * K_EPS)
+            free.release()
         torch.cuda.synchronize()
         n0 = lat.steps_done
-        chunks = max(1, args.steps // K_EPS)
         t = time.perf_counter()
         for j in range(chunks):
             lat.step(K_EPS)                     # ends with a check step: stats D2H
-            jj = (n0 + (j + 1) * K_EPS) // K_EPS
-            lat.set_epsilon(he[jj], hd[jj], n0 + (j + 1) * K_EPS)   # H2D from pinned host
+            slot = ready.get()
+            lat.set_epsilon(st_e_np[slot], st_d_np[slot], n0 + (j + 1) * K_EPS)  # H2D, pinned
+            free.release()
         torch.cuda.synchronize()
         dt = time.perf_counter() - t
+        prod.join()
         e2e = {"value": N * chunks * K_EPS / dt / 1e9, "unit": "GLUPS",
                "h2d_bytes_per_step": 2 * 4 * N / K_EPS,
                "d2h_bytes_per_step": 120 / K_EPS,
-               "note": "phi_ref and d_t phi uploaded from pinned host memory every 10 steps; "
-                       "each 10-step call reads its check statistics back"}
+               "note": "phi_ref and d_t phi uploaded every 10 steps from a ring of pinned staging "
+                       "buffers filled by a host producer thread; each 10-step call reads its check "
+                       "statistics back"}
         lat.close()
     return results, e2e
 

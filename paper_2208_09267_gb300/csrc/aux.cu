@@ -191,8 +191,8 @@ template <class T>
 __global__ void validate_kernel(const T *data, long long n, int unit, long long *first_bad) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const double v = (double)data[i];
-    const bool bad = !isfinite(v) || (unit && !(v > 0.0 && v <= 1.0));
+    const T v = data[i];  // checked in its own type (no conversion on the FP64 pipe)
+    const bool bad = !isfinite(v) || (unit && !(v > T(0) && v <= T(1)));
     if (bad) atomicMin((unsigned long long *)first_bad, (unsigned long long)i);
   }
 }

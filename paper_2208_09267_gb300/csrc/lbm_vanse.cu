@@ -364,17 +364,23 @@ extern "C" int lbm_vanse_create(const lbm_vanse_params *p, lbm_vanse_t *out) {
 // caller's element type into a pitched device buffer of the handle's field
 // type (component a at a*Ni, rows at pitch nxp).  Host sources are copied
 // before the call returns.
+// With sync = false a host source must stay valid until the caller
+// synchronises the stream.
 static int upload_field(lbm_vanse_t h, void *dst, const void *src, int ncomp, int src_is_f64,
-                        int on_device) {
+                        int on_device, bool sync = true) {
   const bool dst_f64 = h->field_elem == 8;
   const int nx = h->p.nx, nxp = h->nxp;
   const long long rows = (long long)h->p.ny * h->p.nz * ncomp;
   const size_t fe = h->field_elem;
   if ((bool)src_is_f64 == dst_f64) {
-    CUDA_TRY(h, cudaMemcpy2DAsync(dst, (size_t)nxp * fe, src, (size_t)nx * fe, (size_t)nx * fe, (size_t)rows,
-                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (nx == nxp)  // unpadded rows: one contiguous copy
+      CUDA_TRY(h, cudaMemcpyAsync(dst, src, (size_t)nx * fe * (size_t)rows, kind, h->stream));
+    else
+      CUDA_TRY(h, cudaMemcpy2DAsync(dst, (size_t)nxp * fe, src, (size_t)nx * fe, (size_t)nx * fe, (size_t)rows,
+                                    kind, h->stream));
     // a pinned host source would be read after the return: wait for the copy
-    if (!on_device) CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (!on_device && sync) CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return LBM_OK;
   }
   if (on_device) {
@@ -411,23 +417,27 @@ static int check_host_values(lbm_vanse_t h, const T *v, long long n, bool unit_i
   return LBM_OK;
 }
 
-// Check an uploaded copy of host values on the device (one scan kernel and a
-// readback of the first bad index); synchronises the stream.
-static int check_uploaded(lbm_vanse_t h, const void *dev, long long n, int is_f64, bool unit_interval,
-                          const char *what) {
+// Check uploaded copies of host values on the device (one scan kernel per
+// field, one readback of the first bad indices); synchronises the stream.
+// Field b may be absent (dev_b null).
+static int check_uploaded2(lbm_vanse_t h, const void *dev_a, bool unit_a, const char *what_a, const void *dev_b,
+                           bool unit_b, const char *what_b, long long n, int is_f64) {
   long long *flag = reinterpret_cast<long long *>(h->stats_dev + 48);
   long long *host = reinterpret_cast<long long *>(h->stats_host + 48);
-  const long long none = n;
-  CUDA_TRY(h, cudaMemcpyAsync(flag, &none, sizeof(none), cudaMemcpyHostToDevice, h->stream));
-  CUDA_TRY(h, lbm::launch_validate(dev, n, is_f64, unit_interval ? 1 : 0, flag, h->stream));
-  CUDA_TRY(h, cudaMemcpyAsync(host, flag, sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
+  // 0x7f.. bytes: a value above every index ("none"); the scan keeps the minimum
+  CUDA_TRY(h, cudaMemsetAsync(flag, 0x7f, 2 * sizeof(long long), h->stream));
+  CUDA_TRY(h, lbm::launch_validate(dev_a, n, is_f64, unit_a ? 1 : 0, flag, h->stream));
+  if (dev_b) CUDA_TRY(h, lbm::launch_validate(dev_b, n, is_f64, unit_b ? 1 : 0, flag + 1, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(host, flag, 2 * sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-  if (*host < n) {
-    // report the caller's dense index of the stored cell
-    const long long i = *host, row = i / h->nxp, x = i % h->nxp;
-    return fail(h, LBM_EINVAL, "%s[%lld] is %s", what, row * h->p.nx + x,
-                unit_interval ? "not finite or outside (0, 1]" : "not finite");
-  }
+  for (int f = 0; f < (dev_b ? 2 : 1); ++f)
+    if (host[f] < n) {
+      // report the caller's dense index of the stored cell
+      const long long i = host[f], row = i / h->nxp, x = i % h->nxp;
+      const bool unit = f == 0 ? unit_a : unit_b;
+      return fail(h, LBM_EINVAL, "%s[%lld] is %s", f == 0 ? what_a : what_b, row * h->p.nx + x,
+                  unit ? "not finite or outside (0, 1]" : "not finite");
+    }
   return LBM_OK;
 }
 
@@ -440,19 +450,21 @@ static int set_epsilon_any(lbm_vanse_t h, const void *eps, const void *deps, lon
   const int dev_f64 = h->field_elem == 8;
   // host values are checked on the device after the upload; nothing of the
   // handle's state changes before both fields passed
-  if ((rc = upload_field(h, h->eps_buf[next], eps, 1, is_f64, on_device))) return rc;
-  if (!on_device && (rc = check_uploaded(h, h->eps_buf[next], h->Ni, dev_f64, true, "eps_ref"))) return rc;
+  // both fields are copied, then checked together with one synchronisation
+  if ((rc = upload_field(h, h->eps_buf[next], eps, 1, is_f64, on_device, false))) return rc;
   if (deps) {
     if (!h->deps) {
       if ((rc = dev_alloc(h, &h->deps, (size_t)h->Ni * h->field_elem))) return rc;
       CUDA_TRY(h, cudaMemsetAsync(h->deps, 0, (size_t)h->Ni * h->field_elem, h->stream));
     }
-    if ((rc = upload_field(h, h->deps, deps, 1, is_f64, on_device))) return rc;
-    if (!on_device && (rc = check_uploaded(h, h->deps, h->Ni, dev_f64, false, "deps_dt"))) return rc;
-    h->h.has_deps = 1;
-  } else {
-    h->h.has_deps = 0;
+    if ((rc = upload_field(h, h->deps, deps, 1, is_f64, on_device, false))) return rc;
   }
+  if (!on_device) {
+    if ((rc = check_uploaded2(h, h->eps_buf[next], true, "eps_ref", deps ? h->deps : nullptr, false, "deps_dt",
+                              h->Ni, dev_f64)))
+      return rc;
+  }
+  h->h.has_deps = deps ? 1 : 0;
   h->eps_cur = next;
   h->h.n_eps = n_ref;
   if (h->p.storage != LBM_FP64) {
