@@ -33,6 +33,7 @@ LatticeDev *handle_device_desc(lbm_vanse_t h);
 const LatticeDev &handle_mirror(lbm_vanse_t h);
 LatticeDev &handle_mirror_mut(lbm_vanse_t h);
 int handle_push(lbm_vanse_t h);
+int handle_push_changed(lbm_vanse_t h, LatticeDev *last, int *pushed);
 cudaStream_t handle_stream(lbm_vanse_t h);
 void set_global_error(const char *msg);
 int sm_count();
@@ -207,6 +208,7 @@ struct HostMember {
   long long budget;
   int type;
   int row_class;  // batched row kernel class, or -1 (one-cell-per-thread tiles)
+  LatticeDev pushed;  // the descriptor as the device holds it (valid after the first push)
   int group;      // parity of the member's time when the row tables were built
   int nrows;      // fluid rows (row members)
   long long last_check_n;
@@ -233,6 +235,7 @@ struct lbm_vanse_batch {
   // (chains present: one character per lane, k*2+red)
   std::map<std::pair<std::string, long long>, cudaGraphExec_t> graphs;
   std::vector<BatchMember> members_host;
+  BatchMember *members_pinned = nullptr;  // max_members: the per-replay upload of the member table
   std::vector<BatchTile> tiles_host;
   std::vector<BatchRange> ranges_host;
   // batched row kernel: class row tables, per-member sums, wait status
@@ -286,6 +289,7 @@ extern "C" int lbm_vanse_batch_create(int max_members, int max_tiles, int tile_c
   if (e == cudaSuccess) e = cudaMalloc(&b->member_sums, sizeof(double) * kRedWidth * max_members);
   if (e == cudaSuccess) e = cudaMalloc(&b->status_dev, sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost(&b->status_host, sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost(&b->members_pinned, sizeof(BatchMember) * max_members);
   if (e == cudaSuccess) e = cudaMemset(b->status_dev, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
   if (e != cudaSuccess) {
@@ -315,6 +319,7 @@ extern "C" void lbm_vanse_batch_destroy(lbm_vanse_batch_t b) {
   cudaFree(b->member_sums);
   cudaFree(b->status_dev);
   if (b->status_host) cudaFreeHost(b->status_host);
+  if (b->members_pinned) cudaFreeHost(b->members_pinned);
   for (int i = 0; i < kLanes; ++i) {
     if (b->side[i]) cudaStreamDestroy(b->side[i]);
     if (b->ev_join[i]) cudaEventDestroy(b->ev_join[i]);
@@ -398,6 +403,19 @@ extern "C" int lbm_vanse_batch_size(lbm_vanse_batch_t b) { return b ? (int)b->me
 // Rebuild and upload the member and tile tables (sorted by type).
 static int upload_tables(lbm_vanse_batch_t b) {
   const int nm = (int)b->members.size();
+  if (!b->dirty) {
+    // membership unchanged: only the budgets move; one asynchronous copy
+    // from pinned memory (the previous replay's copy has completed: its
+    // replay was synchronised)
+    for (int i = 0; i < nm; ++i) {
+      b->members_host[i].budget = b->members[i].budget;
+      b->members_pinned[i] = b->members_host[i];
+    }
+    if (nm && cudaMemcpyAsync(b->members_dev, b->members_pinned, sizeof(BatchMember) * nm, cudaMemcpyHostToDevice,
+                              b->stream) != cudaSuccess)
+      return bfail(LBM_ECUDA, "member table upload failed");
+    return LBM_OK;
+  }
   b->members_host.assign(nm, BatchMember());
   b->tiles_host.clear();
   b->ranges_host.assign(kTypes, BatchRange{0, 0});
@@ -561,8 +579,9 @@ extern "C" int lbm_vanse_batch_step(lbm_vanse_batch_t b, int k, int check) {
   for (auto &hm : b->members) {
     LatticeDev &m = handle_mirror_mut(hm.h);
     m.have_prev = hm.have_prev ? 1 : 0;
-    if ((rc = handle_push(hm.h))) return bfail(rc, "member descriptor upload failed");
-    cudaStreamSynchronize(handle_stream(hm.h));
+    int pushed = 0;
+    if ((rc = handle_push_changed(hm.h, &hm.pushed, &pushed))) return bfail(rc, "member descriptor upload failed");
+    if (pushed || handle_stream(hm.h) != b->stream) cudaStreamSynchronize(handle_stream(hm.h));
     if (hm.row_class >= 0) {
       // members of one class are split by the parity of their time
       const int g = (int)(m.n & 1);
@@ -603,6 +622,9 @@ extern "C" int lbm_vanse_batch_step(lbm_vanse_batch_t b, int k, int check) {
     const long long n_check = m.n + s - 1;
     m.n += s;
     m.sig_rd = m.sig_wr;
+    // the device's copy moved the same way (advance kernel)
+    hm.pushed.n += s;
+    hm.pushed.sig_rd = hm.pushed.sig_wr;
     hm.budget -= s;
     if (check) {
       memcpy(hm.stats, b->out_host + i * kRedWidth, sizeof(hm.stats));

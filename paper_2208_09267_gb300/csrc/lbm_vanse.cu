@@ -978,6 +978,18 @@ LatticeDev *handle_device_desc(lbm_vanse_t h) { return h->d; }
 const LatticeDev &handle_mirror(lbm_vanse_t h) { return h->h; }
 LatticeDev &handle_mirror_mut(lbm_vanse_t h) { return h->h; }
 int handle_push(lbm_vanse_t h) { return push_mirror(h); }
+// Upload the descriptor only if it differs from *last (what the device was
+// last given); *pushed tells whether it did.
+int handle_push_changed(lbm_vanse_t h, LatticeDev *last, int *pushed) {
+  sync_mirror_ptrs(h);
+  *pushed = 0;
+  if (memcmp(&h->h, last, sizeof(LatticeDev)) == 0) return LBM_OK;
+  int rc;
+  if ((rc = push_mirror(h))) return rc;
+  *last = h->h;
+  *pushed = 1;
+  return LBM_OK;
+}
 cudaStream_t handle_stream(lbm_vanse_t h) { return h->stream; }
 void set_global_error(const char *msg) { g_last_error = msg; }
 }  // namespace lbm
