@@ -141,6 +141,24 @@ def eps_fields(L, t):
     return e.ravel().astype(np.float32), d.ravel().astype(np.float32)
 
 
+def max_over_ranks(value: float, device) -> float:
+    """The largest value over the ranks of the process group (the job's
+    time is its slowest rank's); the value itself with one rank."""
+    import torch
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_glups(cells_per_rank: int, steps: int, max_ms: float, world: int) -> float:
+    """Whole-job throughput: every rank advances its own replica of
+    cells_per_rank cells by `steps` steps; the job takes the slowest rank's
+    time (weak scaling, no data-path collective)."""
+    return cells_per_rank * world * steps / (max_ms * 1e-3) / 1e9
+
+
 def run_gpu(args, rank, world):
     import torch
 
@@ -218,9 +236,7 @@ def run_gpu(args, rank, world):
         step_ms = sum(a.elapsed_time(b) for a, b, _ in ev)
         nk = sum(k for _, _, k in ev)
         if world > 1:
-            t = torch.tensor([total_ms], device=f"cuda:{dev}")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(t.item())
+            total_ms = max_over_ranks(total_ms, f"cuda:{dev}")
         st = lat.step(1)  # one check step (not timed) to confirm the run is sane
         if st["nan_seen"]:
             raise RuntimeError(f"{storage}: NaN after the timed steps")
@@ -514,7 +530,7 @@ def main():
     res, e2e = run_gpu(args, rank, world)
     main_st = args.storages[0]
     r = res[main_st]
-    glups = N / (r["total_ms"] / args.steps) / 1e6 * world
+    glups = aggregate_glups(N, args.steps, r["total_ms"], world)
     peak, peak_kind = peak_hbm()
     bpc = bytes_per_cell(main_st)
     achieved = bpc * N / (r["kernel_ms"] * 1e-3) / 1e9

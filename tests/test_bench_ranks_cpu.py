@@ -1,0 +1,58 @@
+"""The multi-rank host logic of bench.py on CPU: two gloo ranks, each with
+its own replica timing; the job's time is the slowest rank's and the
+throughput counts the cells of every rank (weak scaling)."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+from conftest import ROOT
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, times, out):
+    import sys
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        m = bench.max_over_ranks(times[rank], "cpu")
+        out[rank] = (m, bench.aggregate_glups(1000, 10, m, world))
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_slowest_time():
+    ctx = mp.get_context("spawn")
+    manager = ctx.Manager()
+    out = manager.dict()
+    times = [2.0, 5.0]
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, times, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    for r in range(2):
+        m, g = out[r]
+        assert m == 5.0
+        # 2 ranks x 1000 cells x 10 steps in 5 ms
+        assert g == pytest.approx(2 * 1000 * 10 / 5e-3 / 1e9)
+
+
+def test_one_rank_without_a_process_group():
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(3.5, "cpu") == 3.5
+    assert bench.aggregate_glups(16777216, 1000, 500.0, 1) == pytest.approx(16777216 * 1000 / 0.5 / 1e9)
