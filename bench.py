@@ -364,7 +364,7 @@ def run_porous(steps=200, warmup=10, shape=(512, 256, 256), storages=("fp32", "f
     return out
 
 
-def run_batched(count=64, steps=200, storages=("fp16", "fp32")):
+def run_batched(count=256, steps=200, storages=("fp16", "fp32")):
     """Many independent lattices (half D2Q9 squares of side 32..512, half
     D3Q19 cubes of side 32..128, product-sine phi, tau in [0.55, 1.2]) advanced
     together by the batched graph-captured kernels, against the plain
@@ -493,7 +493,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-porous", action="store_true")
     ap.add_argument("--porous-steps", type=int, default=200)
-    ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--serve-count", type=int, default=48)
     ap.add_argument("--serve-rate", type=float, default=100.0)
