@@ -255,7 +255,12 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
                                                  int x, RedAcc &acc) {
   using Lay = RowLayout<LAT, ST, ODD, PITCH>;
   constexpr int Q = LAT::Q, D = LAT::D;
-  constexpr bool kScaled = sizeof(ST) < 4;  // FP16 stores deviations times 2^k
+  // FP16 stores deviations times 2^k.  The update below runs in those
+  // storage units (d, the sums and the collision output all times 2^k): a
+  // power of two scales every rounding exactly, so the stored results are
+  // those of the unscaled arithmetic, without a multiply per population on
+  // load and store.
+  constexpr bool kScaled = sizeof(ST) < 4;
   const int nx = L.nx;
   const ST *prow = reinterpret_cast<const ST *>(stage);
   const __half *srow = reinterpret_cast<const __half *>(stage + Lay::kSigOff);
@@ -289,10 +294,11 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
   // the cell's frame: its own shift as stored (sigma_rd)
   const float s_x = rho0 * (reshift ? __half2float(srd[cell]) : sig_own);
 
-  // 1. decode: d_i = f_i/w_i - s_x.  A value stored in another cell m carries
-  //    that cell's shift: add delta_i = rho0 sigma(m) - s_x (exact product in
-  //    the FMA; the encode below uses the same form, so the round trip is
-  //    exact up to the final rounding).  Own-cell values need no shift.
+  // 1. decode: d_i = f_i/w_i - s_x (in storage units).  A value stored in
+  //    another cell m carries that cell's shift: add delta_i = rho0 sigma(m)
+  //    - s_x (exact product in the FMA; the encode below uses the same form,
+  //    so the round trip is exact up to the final rounding).  Own-cell values
+  //    need no shift.
   float d[Q], delta[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
@@ -301,13 +307,13 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
     const float q = PopIO<ST>::ld(prow + i * PITCH + (own ? x : xs[1 - cx]));
     if (own) {
       delta[i] = 0.f;
-      d[i] = kScaled ? q * inv_scale : q;
+      d[i] = q;
     } else {
       const float sm =
           reshift ? __half2float(srd[rc.base[1 - cz][1 - cy] + xs[1 - cx]]) : SIG_AT(-cy, -cz, xs[1 - cx]);
       delta[i] = fmaf(rho0, sm, -s_x);
-      // q 2^-k is exact, so the FMA rounds once, as q 2^-k + delta does
-      d[i] = kScaled ? fmaf(q, inv_scale, delta[i]) : q + delta[i];
+      // delta 2^k is exact, so the FMA rounds once, as q + delta 2^k does
+      d[i] = kScaled ? fmaf(delta[i], scale, q) : q + delta[i];
     }
   }
 
@@ -320,6 +326,12 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
     if (LAT::c(i, 0) != 0) j0 = fmaf(LAT::c(i, 0) > 0 ? w : -w, d[i], j0);
     if (LAT::c(i, 1) != 0) j1 = fmaf(LAT::c(i, 1) > 0 ? w : -w, d[i], j1);
     if (D == 3 && LAT::c(i, 2) != 0) j2 = fmaf(LAT::c(i, 2) > 0 ? w : -w, d[i], j2);
+  }
+  if (kScaled) {
+    dM *= inv_scale;
+    j0 *= inv_scale;
+    j1 *= inv_scale;
+    j2 *= inv_scale;
   }
   const float M0 = s_x + dM;
 
@@ -409,12 +421,15 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
   //   shift difference of the neighbour x + xi_i is -delta of the opposite
   //   direction.
   const float m15usq = -1.5f * usq;
-  const float m3uF = -cf3 * uF;
+  // coefficients of the collision output, in storage units
+  const float sc = kScaled ? scale : 1.0f;
+  const float omega_s = omega * sc, cf3_s = cf3 * sc, cf9_s = cf9 * sc;
+  const float m3uF_s = (-cf3 * uF) * sc;
   const float enc_own = reshift ? fmaf(-rho0, sig_own, s_x) : 0.f;
   SRng rng((unsigned)cell, n);
   const bool sr = L.fp16_nearest == 0;
   // encode population i (compile-time index) with post-collision deviation
-  // DSTAR: P_ = its slot, V_ = the value to store (scaled for FP16)
+  // DSTAR (storage units): P_ = its slot, V_ = the value to store
 #define ENCODE_POP(i, DSTAR, P_, V_)                                                               \
   ST *P_;                                                                                          \
   float V_;                                                                                        \
@@ -422,7 +437,7 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
     const int cx_ = LAT::c((i), 0), cy_ = LAT::c((i), 1), cz_ = LAT::c((i), 2);                    \
     const float ds_ = (DSTAR);                                                                     \
     if (OWN_DST(i)) {                                                                              \
-      V_ = ds_ + enc_own;                                                                          \
+      V_ = reshift ? fmaf(enc_own, sc, ds_) : ds_;                                                 \
       P_ = pop + opp_of(i) * plane + cell;                                                         \
     } else {                                                                                       \
       const int xm_ = xs[1 + cx_];                                                                 \
@@ -431,20 +446,19 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
         enc_ = -delta[opp_of(i)];                                                                  \
       else                                                                                         \
         enc_ = fmaf(-rho0, SIG_AT(cy_, cz_, xm_), s_x);                                            \
-      V_ = ds_ + enc_;                                                                             \
+      V_ = fmaf(enc_, sc, ds_);                                                                    \
       P_ = pop + (i) * plane + rc.base[1 + cz_][1 + cy_] + xm_;                                    \
     }                                                                                              \
-    if (kScaled) V_ *= scale;                                                                      \
   }
   // rest population: cu = cF = 0
   {
-    ENCODE_POP(0, fmaf(om1, d[0], fmaf(omega, fmaf(M0, m15usq, dM), m3uF)), p0_, v0_);
+    ENCODE_POP(0, fmaf(om1, d[0], fmaf(omega_s, fmaf(M0, m15usq, dM), m3uF_s)), p0_, v0_);
     store_pop<ST>(p0_, v0_, rng, sr);
   }
   // opposite pairs (i, i+1): cu and cF change sign, so
   //   omega d^eq + Omega = A +- B,  A = omega (dM + M0 (4.5 cu^2 - 1.5 u.u)) + cf (9 cu cF - 3 u.F),
   //                                 B = 3 omega M0 cu + 3 cf cF
-  const float oM03 = 3.0f * omega * M0;
+  const float oM03 = 3.0f * omega_s * M0;
 #pragma unroll
   for (int i = 1; i < Q; i += 2) {
     const int cx = LAT::c(i, 0), cy = LAT::c(i, 1), cz = LAT::c(i, 2);
@@ -456,8 +470,8 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
     if (cz == 1) { cu += u2; cF += F2; }
     if (cz == -1) { cu -= u2; cF -= F2; }
     const float t = fmaf(M0, fmaf(4.5f * cu, cu, m15usq), dM);
-    const float A = fmaf(omega, t, fmaf(cf9 * cu, cF, m3uF));
-    const float B = fmaf(oM03, cu, cf3 * cF);
+    const float A = fmaf(omega_s, t, fmaf(cf9_s * cu, cF, m3uF_s));
+    const float B = fmaf(oM03, cu, cf3_s * cF);
     ENCODE_POP(i, fmaf(om1, d[i], A + B), pa_, va_);
     ENCODE_POP(i + 1, fmaf(om1, d[i + 1], A - B), pb_, vb_);
     store_pop_pair<ST>(pa_, va_, pb_, vb_, rng, sr);
