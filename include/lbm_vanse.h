@@ -146,9 +146,10 @@ LBM_API const char *lbm_vanse_last_error(lbm_vanse_t h);
 LBM_API int lbm_vanse_params_default(lbm_vanse_params *p);
 
 /* Device bytes a handle with these parameters allocates (populations,
-   phi double buffer, d_t phi, force fields are counted as allocated
-   lazily: this is the figure without optional fields, plus the moment and
-   reduction scratch).  Used for admission by HBM budget. */
+   phi double buffer, shift double buffer, and with_deps / with_force_field:
+   the d_t phi double buffer and the force fields, which are allocated
+   lazily; plus the moment and reduction scratch).  Used for admission by
+   HBM budget. */
 LBM_API size_t lbm_vanse_device_bytes(const lbm_vanse_params *p, int with_deps, int with_force_field);
 
 /* Create a lattice in the rest state u = 0, p = 0 with phi = 1 everywhere:
@@ -169,12 +170,39 @@ LBM_API void lbm_vanse_destroy(lbm_vanse_t h);
    decodes with the previous sigma and encodes with the new one, so no extra
    pass over the populations runs.
    Errors: LBM_EINVAL if a host-side eps_ref value is not in (0, 1] or not
-   finite (device-side inputs are not validated).  The FP64 twin takes
-   doubles; on FP32/FP16 handles it rounds them to float. */
+   finite, or a host-side deps_dt value is not finite (device-side inputs
+   are not validated); a failed call leaves both fields as they were.
+   LBM_ESTATE while a staged refresh awaits its commit (below).  The FP64
+   twin takes doubles; on FP32/FP16 handles it rounds them to float. */
 LBM_API int lbm_vanse_set_epsilon(lbm_vanse_t h, const float *eps_ref, const float *deps_dt,
                           long long n_ref, int on_device);
 LBM_API int lbm_vanse_set_epsilon_f64(lbm_vanse_t h, const double *eps_ref, const double *deps_dt,
                               long long n_ref, int on_device);
+
+/* The same refresh of phi(x, t) = eps_ref(x) + (t - n_ref) deps_dt(x)
+   (Sec. 2.2) in two calls, so that its upload overlaps the steps between
+   them.  lbm_vanse_stage_epsilon starts copying eps_ref and deps_dt (FP32,
+   N values each, dense, x fastest; deps_dt NULL = static phi; on_device as
+   in lbm_vanse_set_epsilon) into the handle's spare phi buffers on a copy
+   stream of its own and returns without waiting; host values are then
+   scanned there.  Steps issued meanwhile use the current phi.
+   lbm_vanse_commit_epsilon waits for the copy and, if the values passed,
+   makes them current: the state afterwards is bit for bit the one that
+   lbm_vanse_set_epsilon(h, eps_ref, deps_dt, n_ref, on_device) called at
+   the commit gives.
+   Ownership: the caller's buffers are read asynchronously and must stay
+   valid and unchanged until lbm_vanse_commit_epsilon returns (pinned host
+   memory lets the copy overlap the steps).
+   Errors: stage: LBM_EINVAL (NULL handle or eps_ref, FP64 storage),
+   LBM_ESTATE (a staged refresh already awaits its commit), LBM_ENOMEM,
+   LBM_ECUDA.  commit: LBM_ESTATE (nothing staged), LBM_EINVAL (a host value
+   of eps_ref is not in (0, 1] or not finite, or one of deps_dt is not
+   finite: the refresh is dropped and the lattice is unchanged), LBM_ECUDA.
+   While a refresh is staged, lbm_vanse_set_epsilon, its FP64 twin and
+   lbm_vanse_load_state return LBM_ESTATE. */
+LBM_API int lbm_vanse_stage_epsilon(lbm_vanse_t h, const float *eps_ref, const float *deps_dt,
+                            long long n_ref, int on_device);
+LBM_API int lbm_vanse_commit_epsilon(lbm_vanse_t h);
 
 /* External force density: sum_k F_k = g + field(x) + (t - n_ref) dfield_dt(x)
    + F_PC (Sec. 2.2 eq. (pressForce); Sec. 3, force sum of the manufactured

@@ -43,7 +43,7 @@ struct lbm_vanse {
   void *eps_buf[2] = {nullptr, nullptr};
   __half *sig_buf[2] = {nullptr, nullptr};  // shift sigma of each phi_ref buffer
   int eps_cur = 0;
-  void *deps = nullptr;
+  void *deps_buf[2] = {nullptr, nullptr};  // d_t phi beside each phi_ref buffer
   void *force = nullptr, *dforce = nullptr;
   float *u_prev = nullptr;
   double *partials = nullptr;
@@ -56,6 +56,13 @@ struct lbm_vanse {
   std::map<std::tuple<int, int>, cudaGraphExec_t> graphs;  // (parity, steps)
   std::string err;
   size_t field_elem = 4;  // bytes of one phi / force value on the device
+  // a phi refresh staged into the spare buffers (lbm_vanse_stage_epsilon)
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_order = nullptr, ev_staged = nullptr;
+  int staged = 0;          // awaits lbm_vanse_commit_epsilon
+  int staged_deps = 0;     // carries d_t phi
+  int staged_checked = 0;  // host values: scanned on the copy stream
+  long long staged_n_ref = 0;
 };
 
 // ---------------------------------------------------------------- errors
@@ -156,7 +163,7 @@ extern "C" size_t lbm_vanse_device_bytes(const lbm_vanse_params *p, int with_dep
   size_t b = (size_t)Q * plane_of(N) * kElem[p->storage];  // populations
   b += 2 * (size_t)N * fe;                                  // phi double buffer
   if (p->storage != LBM_FP64) b += 2 * (size_t)N * 2;       // shift double buffer
-  if (with_deps) b += (size_t)N * fe;
+  if (with_deps) b += 2 * (size_t)N * fe;                   // d_t phi double buffer
   if (with_force_field) b += 2 * 3 * (size_t)N * fe;
   const lbm::StepLaunch ls = lbm::make_launch(p->nx, p->ny, p->nz, p->block_x, p->block_y);
   size_t nb = (size_t)ls.grid.x * ls.grid.y * ls.grid.z;
@@ -178,7 +185,7 @@ static void sync_mirror_ptrs(lbm_vanse_t h) {
   m.cff = (float)m.cf;
   h->h.pop = h->pop;
   h->h.eps = h->eps_buf[h->eps_cur];
-  h->h.deps = h->h.has_deps ? h->deps : nullptr;
+  h->h.deps = h->h.has_deps ? h->deps_buf[h->eps_cur] : nullptr;
   h->h.force = h->h.has_force ? h->force : nullptr;
   h->h.dforce = h->h.has_dforce ? h->dforce : nullptr;
   h->h.partials = h->partials;
@@ -201,12 +208,18 @@ extern "C" void lbm_vanse_destroy(lbm_vanse_t h) {
   if (!h) return;
   free_graphs(h);
   cudaStream_t s = h->stream;
-  void *ptrs[] = {h->pop, h->eps_buf[0], h->eps_buf[1], h->sig_buf[0], h->sig_buf[1], h->deps, h->force,
-                  h->dforce, h->u_prev, h->partials, h->stats_dev, h->status, h->d};
+  // a staged copy may still be writing the spare buffers
+  if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);
+  void *ptrs[] = {h->pop,       h->eps_buf[0], h->eps_buf[1], h->sig_buf[0], h->sig_buf[1],
+                  h->deps_buf[0], h->deps_buf[1], h->force,     h->dforce,     h->u_prev,
+                  h->partials,  h->stats_dev,  h->status,    h->d};
   for (void *q : ptrs)
     if (q) cudaFreeAsync(q, s);
   if (h->stats_host) cudaFreeHost(h->stats_host);
   cudaStreamSynchronize(s);
+  if (h->ev_order) cudaEventDestroy(h->ev_order);
+  if (h->ev_staged) cudaEventDestroy(h->ev_staged);
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
   delete h;
 }
 
@@ -441,30 +454,21 @@ static int check_uploaded2(lbm_vanse_t h, const void *dev_a, bool unit_a, const 
   return LBM_OK;
 }
 
-static int set_epsilon_any(lbm_vanse_t h, const void *eps, const void *deps, long long n_ref,
-                           int on_device, int is_f64) {
-  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
-  if (!eps) return fail(h, LBM_EINVAL, "eps_ref is NULL");
+// d_t phi buffer b, allocated on first use and zeroed (the row padding must
+// pass the finite-value check of later uploads).
+static int ensure_deps_buf(lbm_vanse_t h, int b) {
+  if (h->deps_buf[b]) return LBM_OK;
   int rc;
-  const int next = 1 - h->eps_cur;
-  const int dev_f64 = h->field_elem == 8;
-  // host values are checked on the device after the upload; nothing of the
-  // handle's state changes before both fields passed
-  // both fields are copied, then checked together with one synchronisation
-  if ((rc = upload_field(h, h->eps_buf[next], eps, 1, is_f64, on_device, false))) return rc;
-  if (deps) {
-    if (!h->deps) {
-      if ((rc = dev_alloc(h, &h->deps, (size_t)h->Ni * h->field_elem))) return rc;
-      CUDA_TRY(h, cudaMemsetAsync(h->deps, 0, (size_t)h->Ni * h->field_elem, h->stream));
-    }
-    if ((rc = upload_field(h, h->deps, deps, 1, is_f64, on_device, false))) return rc;
-  }
-  if (!on_device) {
-    if ((rc = check_uploaded2(h, h->eps_buf[next], true, "eps_ref", deps ? h->deps : nullptr, false, "deps_dt",
-                              h->Ni, dev_f64)))
-      return rc;
-  }
-  h->h.has_deps = deps ? 1 : 0;
+  if ((rc = dev_alloc(h, &h->deps_buf[b], (size_t)h->Ni * h->field_elem))) return rc;
+  CUDA_TRY(h, cudaMemsetAsync(h->deps_buf[b], 0, (size_t)h->Ni * h->field_elem, h->stream));
+  return LBM_OK;
+}
+
+// Make the spare phi_ref / d_t phi buffers (already filled and checked) the
+// current ones: the shift sigma of the new phi_ref is computed into the
+// spare shift buffer, and the next step decodes with the old one.
+static int adopt_epsilon(lbm_vanse_t h, int next, int has_deps, long long n_ref) {
+  h->h.has_deps = has_deps;
   h->eps_cur = next;
   h->h.n_eps = n_ref;
   if (h->p.storage != LBM_FP64) {
@@ -476,6 +480,29 @@ static int set_epsilon_any(lbm_vanse_t h, const void *eps, const void *deps, lon
   return push_mirror(h);
 }
 
+static int set_epsilon_any(lbm_vanse_t h, const void *eps, const void *deps, long long n_ref,
+                           int on_device, int is_f64) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (!eps) return fail(h, LBM_EINVAL, "eps_ref is NULL");
+  if (h->staged) return fail(h, LBM_ESTATE, "a staged phi refresh awaits lbm_vanse_commit_epsilon");
+  int rc;
+  const int next = 1 - h->eps_cur;
+  const int dev_f64 = h->field_elem == 8;
+  // both fields go to the spare buffers and are checked together with one
+  // synchronisation; nothing the lattice uses changes before both passed
+  if ((rc = upload_field(h, h->eps_buf[next], eps, 1, is_f64, on_device, false))) return rc;
+  if (deps) {
+    if ((rc = ensure_deps_buf(h, next))) return rc;
+    if ((rc = upload_field(h, h->deps_buf[next], deps, 1, is_f64, on_device, false))) return rc;
+  }
+  if (!on_device) {
+    if ((rc = check_uploaded2(h, h->eps_buf[next], true, "eps_ref", deps ? h->deps_buf[next] : nullptr, false,
+                              "deps_dt", h->Ni, dev_f64)))
+      return rc;
+  }
+  return adopt_epsilon(h, next, deps ? 1 : 0, n_ref);
+}
+
 extern "C" int lbm_vanse_set_epsilon(lbm_vanse_t h, const float *eps_ref, const float *deps_dt,
                                      long long n_ref, int on_device) {
   return set_epsilon_any(h, eps_ref, deps_dt, n_ref, on_device, 0);
@@ -484,6 +511,87 @@ extern "C" int lbm_vanse_set_epsilon(lbm_vanse_t h, const float *eps_ref, const 
 extern "C" int lbm_vanse_set_epsilon_f64(lbm_vanse_t h, const double *eps_ref, const double *deps_dt,
                                          long long n_ref, int on_device) {
   return set_epsilon_any(h, eps_ref, deps_dt, n_ref, on_device, 1);
+}
+
+// One dense FP32 field into the pitched buffer dst on stream cs, not waited for.
+static int copy_field_async(lbm_vanse_t h, void *dst, const float *src, int on_device, cudaStream_t cs) {
+  const int nx = h->p.nx, nxp = h->nxp;
+  const size_t rows = (size_t)h->p.ny * h->p.nz;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (nx == nxp)
+    CUDA_TRY(h, cudaMemcpyAsync(dst, src, (size_t)nx * 4 * rows, kind, cs));
+  else
+    CUDA_TRY(h, cudaMemcpy2DAsync(dst, (size_t)nxp * 4, src, (size_t)nx * 4, (size_t)nx * 4, rows, kind, cs));
+  return LBM_OK;
+}
+
+static int stage_epsilon_impl(lbm_vanse_t h, const float *eps, const float *deps, long long n_ref,
+                              int on_device) {
+  int rc;
+  if (!h->copy_stream) {
+    CUDA_TRY(h, cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+    CUDA_TRY(h, cudaEventCreateWithFlags(&h->ev_order, cudaEventDisableTiming));
+    CUDA_TRY(h, cudaEventCreateWithFlags(&h->ev_staged, cudaEventDisableTiming));
+  }
+  const int next = 1 - h->eps_cur;
+  if (deps && (rc = ensure_deps_buf(h, next))) return rc;
+  // the spare buffers were last read by work already on the handle's stream
+  // (the steps before the previous refresh): the copies start after it
+  CUDA_TRY(h, cudaEventRecord(h->ev_order, h->stream));
+  CUDA_TRY(h, cudaStreamWaitEvent(h->copy_stream, h->ev_order, 0));
+  if ((rc = copy_field_async(h, h->eps_buf[next], eps, on_device, h->copy_stream))) return rc;
+  if (deps && (rc = copy_field_async(h, h->deps_buf[next], deps, on_device, h->copy_stream))) return rc;
+  if (!on_device) {
+    // the same scan as set_epsilon's, on the copy stream, into its own slots
+    long long *flag = reinterpret_cast<long long *>(h->stats_dev + 56);
+    CUDA_TRY(h, cudaMemsetAsync(flag, 0x7f, 2 * sizeof(long long), h->copy_stream));
+    CUDA_TRY(h, lbm::launch_validate(h->eps_buf[next], h->Ni, 0, 1, flag, h->copy_stream));
+    if (deps) CUDA_TRY(h, lbm::launch_validate(h->deps_buf[next], h->Ni, 0, 0, flag + 1, h->copy_stream));
+    CUDA_TRY(h, cudaMemcpyAsync(h->stats_host + 56, flag, 2 * sizeof(long long), cudaMemcpyDeviceToHost,
+                                h->copy_stream));
+  }
+  CUDA_TRY(h, cudaEventRecord(h->ev_staged, h->copy_stream));
+  h->staged = 1;
+  h->staged_deps = deps ? 1 : 0;
+  h->staged_checked = on_device ? 0 : 1;
+  h->staged_n_ref = n_ref;
+  return LBM_OK;
+}
+
+extern "C" int lbm_vanse_stage_epsilon(lbm_vanse_t h, const float *eps_ref, const float *deps_dt,
+                                       long long n_ref, int on_device) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (!eps_ref) return fail(h, LBM_EINVAL, "eps_ref is NULL");
+  if (h->field_elem != 4)
+    return fail(h, LBM_EINVAL, "staged phi refreshes need FP32 fields (FP32 or FP16 storage)");
+  if (h->staged) return fail(h, LBM_ESTATE, "a staged phi refresh already awaits lbm_vanse_commit_epsilon");
+  const int rc = stage_epsilon_impl(h, eps_ref, deps_dt, n_ref, on_device);
+  if (rc != LBM_OK && h->copy_stream) {
+    // nothing may still write the spare buffers after a failed call
+    cudaStreamSynchronize(h->copy_stream);
+    h->staged = 0;
+  }
+  return rc;
+}
+
+extern "C" int lbm_vanse_commit_epsilon(lbm_vanse_t h) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (!h->staged) return fail(h, LBM_ESTATE, "no staged phi refresh to commit");
+  h->staged = 0;
+  CUDA_TRY(h, cudaEventSynchronize(h->ev_staged));
+  if (h->staged_checked) {
+    const long long *host = reinterpret_cast<const long long *>(h->stats_host + 56);
+    for (int f = 0; f < (h->staged_deps ? 2 : 1); ++f)
+      if (host[f] < h->Ni) {
+        // the caller's dense index of the stored cell
+        const long long i = host[f], row = i / h->nxp, x = i % h->nxp;
+        return fail(h, LBM_EINVAL, "%s[%lld] is %s", f == 0 ? "eps_ref" : "deps_dt", row * h->p.nx + x,
+                    f == 0 ? "not finite or outside (0, 1]" : "not finite");
+      }
+  }
+  // the handle's stream reads the new fields only after the copies
+  CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->ev_staged, 0));
+  return adopt_epsilon(h, 1 - h->eps_cur, h->staged_deps, h->staged_n_ref);
 }
 
 static int set_force_any(lbm_vanse_t h, const double *g, const void *field, const void *dfield,
@@ -904,7 +1012,8 @@ extern "C" int lbm_vanse_save_state(lbm_vanse_t h, void *buf, size_t *size) {
   o += fb;
   if (sb) CUDA_TRY(h, cudaMemcpyAsync(o, h->h.sig_rd, sb, cudaMemcpyDeviceToHost, h->stream));
   o += sb;
-  if (h->h.has_deps) CUDA_TRY(h, cudaMemcpyAsync(o, h->deps, fb, cudaMemcpyDeviceToHost, h->stream));
+  if (h->h.has_deps)
+    CUDA_TRY(h, cudaMemcpyAsync(o, h->deps_buf[h->eps_cur], fb, cudaMemcpyDeviceToHost, h->stream));
   o += fb;
   if (h->h.has_force) CUDA_TRY(h, cudaMemcpyAsync(o, h->force, 3 * fb, cudaMemcpyDeviceToHost, h->stream));
   o += 3 * fb;
@@ -917,6 +1026,7 @@ extern "C" int lbm_vanse_save_state(lbm_vanse_t h, void *buf, size_t *size) {
 extern "C" int lbm_vanse_load_state(lbm_vanse_t h, const void *buf, size_t size) {
   if (!h || !buf) return fail(h, LBM_EINVAL, "NULL argument");
   if (size < sizeof(StateHeader)) return fail(h, LBM_EINVAL, "buffer too small");
+  if (h->staged) return fail(h, LBM_ESTATE, "a staged phi refresh awaits lbm_vanse_commit_epsilon");
   StateHeader hd;
   memcpy(&hd, buf, sizeof(hd));
   const size_t pop_bytes = (size_t)h->Q * h->h.plane * kElem[h->p.storage];
@@ -939,8 +1049,8 @@ extern "C" int lbm_vanse_load_state(lbm_vanse_t h, const void *buf, size_t size)
   o += sb;
   h->eps_cur = cur;
   if (hd.has_deps) {
-    if (!h->deps && (rc = dev_alloc(h, &h->deps, fb))) return rc;
-    CUDA_TRY(h, cudaMemcpyAsync(h->deps, o, fb, cudaMemcpyHostToDevice, h->stream));
+    if ((rc = ensure_deps_buf(h, cur))) return rc;
+    CUDA_TRY(h, cudaMemcpyAsync(h->deps_buf[cur], o, fb, cudaMemcpyHostToDevice, h->stream));
   }
   o += fb;
   if (hd.has_force) {

@@ -73,6 +73,8 @@ _SIGS = {
     "lbm_vanse_destroy": (None, [_H]),
     "lbm_vanse_set_epsilon": (ctypes.c_int, [_H, _P, _P, ctypes.c_longlong, ctypes.c_int]),
     "lbm_vanse_set_epsilon_f64": (ctypes.c_int, [_H, _P, _P, ctypes.c_longlong, ctypes.c_int]),
+    "lbm_vanse_stage_epsilon": (ctypes.c_int, [_H, _P, _P, ctypes.c_longlong, ctypes.c_int]),
+    "lbm_vanse_commit_epsilon": (ctypes.c_int, [_H]),
     "lbm_vanse_set_force": (ctypes.c_int, [_H, _P, _P, _P, ctypes.c_longlong, ctypes.c_int]),
     "lbm_vanse_set_force_f64": (ctypes.c_int, [_H, _P, _P, _P, ctypes.c_longlong, ctypes.c_int]),
     "lbm_vanse_init_equilibrium": (ctypes.c_int, [_H, _P, _P, ctypes.c_int, ctypes.c_int]),
@@ -220,6 +222,7 @@ class Lattice:
         if getattr(self, "_h", None):
             lib().lbm_vanse_destroy(self._h)
             self._h = None
+        self._staged = None
 
     def __del__(self):
         try:
@@ -247,6 +250,23 @@ class Lattice:
         dev = _same_device_kind(a, b)
         fn = lib().lbm_vanse_set_epsilon_f64 if f64 else lib().lbm_vanse_set_epsilon
         _check(fn(self.handle, a[0], b[0], int(n_ref), dev), self.handle)
+
+    def stage_epsilon(self, eps_ref, deps_dt=None, n_ref=0):
+        """Start the upload of a phi refresh (FP32 values) on the library's
+        copy stream; steps issued before commit_epsilon() overlap it.  The
+        arrays are kept alive here until the commit."""
+        a = _arg(eps_ref, self.n, False, "eps_ref")
+        b = _arg(deps_dt, self.n, False, "deps_dt")
+        dev = _same_device_kind(a, b)
+        _check(lib().lbm_vanse_stage_epsilon(self.handle, a[0], b[0], int(n_ref), dev), self.handle)
+        self._staged = (a[2], b[2])
+
+    def commit_epsilon(self):
+        """Make the staged refresh current (as set_epsilon would)."""
+        try:
+            _check(lib().lbm_vanse_commit_epsilon(self.handle), self.handle)
+        finally:
+            self._staged = None
 
     def set_force(self, g=(0.0, 0.0, 0.0), field=None, dfield_dt=None, n_ref=0, f64=None):
         f64 = self.f64 if f64 is None else f64
