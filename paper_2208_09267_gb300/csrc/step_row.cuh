@@ -273,7 +273,10 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
   // shift changed by the last set_epsilon
   const bool reshift = RS == 2 ? srd != L.sig_wr : RS == 1;
   ST *__restrict__ pop = static_cast<ST *>(L.pop);
-  const int plane = (int)L.plane;
+  // plane i starts i * plane elements into pop: a 64-bit offset (Q planes of
+  // up to 2^31 stored cells pass the int range); offsets within a plane are
+  // ints (fewer than 2^31 stored cells)
+  const long long plane = L.plane;
   const float omega = L.omegaf;
   const float om1 = 1.0f - omega;
   const float cf3 = L.cf3f, cf9 = L.cf9f;
@@ -367,7 +370,7 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
   float F2 = D == 3 ? fmaf(pc2, e_zp - e_zm, L.gf[2]) : 0.f;
   if (L.has_force) {
     const float *__restrict__ fo = static_cast<const float *>(L.force);
-    const int N = (int)L.ncell;
+    const long long N = L.ncell;
     float a0 = __ldg(fo + cell), a1 = __ldg(fo + N + cell), a2 = D == 3 ? __ldg(fo + 2 * N + cell) : 0.f;
     if (L.has_dforce) {
       const float *__restrict__ df = static_cast<const float *>(L.dforce);
@@ -396,7 +399,7 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
     acc.v[5] += (double)usq;
     if (L.u_prev) {
       float *up = L.u_prev;
-      const int N = (int)L.ncell;
+      const long long N = L.ncell;
       if (L.have_prev) {
         const double a = (double)u0 - (double)up[cell];
         const double b = (double)u1 - (double)up[N + cell];
@@ -438,7 +441,7 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
     const float ds_ = (DSTAR);                                                                     \
     if (OWN_DST(i)) {                                                                              \
       V_ = reshift ? fmaf(enc_own, sc, ds_) : ds_;                                                 \
-      P_ = pop + opp_of(i) * plane + cell;                                                         \
+      P_ = (pop + opp_of(i) * plane) + cell;                                                       \
     } else {                                                                                       \
       const int xm_ = xs[1 + cx_];                                                                 \
       float enc_;                                                                                  \
@@ -447,7 +450,7 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
       else                                                                                         \
         enc_ = fmaf(-rho0, SIG_AT(cy_, cz_, xm_), s_x);                                            \
       V_ = fmaf(enc_, sc, ds_);                                                                    \
-      P_ = pop + (i) * plane + rc.base[1 + cz_][1 + cy_] + xm_;                                    \
+      P_ = (pop + (i) * plane) + (rc.base[1 + cz_][1 + cy_] + xm_);                                \
     }                                                                                              \
   }
   // rest population: cu = cF = 0

@@ -390,3 +390,39 @@ def test_row_kernel_wait_limit_reports_timeout():
     lat.init_equilibrium()
     st = lat.step(4)
     assert not st["nan_seen"] and st["mass"] > 0
+
+
+def test_row_kernel_addresses_planes_past_the_int_range():
+    """D3Q19 FP32 at 512^3 (134 M cells): population plane 16 starts 2^31
+    elements into the array, so the row kernel's stores must address the
+    planes in 64 bits.  One even and one odd step of the row kernel give the
+    moments of the one-cell-per-thread kernel (64-bit indices throughout) to
+    float rounding, and the same mass.  Fields stay on the device."""
+    import torch
+    n = 512
+    N = n ** 3
+    assert 16 * N >= 2 ** 31
+    ax = torch.arange(n, device="cuda", dtype=torch.float32) * (2.0 * np.pi / n)
+    s = torch.sin(ax)
+    eps = (0.8 + 0.15 * s[:, None, None] * s[None, :, None] * torch.cos(ax)[None, None, :]).reshape(-1)
+    out = {}
+    for kern in ("row", "cell"):
+        lat = lbm.Lattice("D3Q19", (n, n, n), tau=0.6, storage="fp32", kernel=kern)
+        assert lat.row_kernel == (kern == "row")
+        lat.set_epsilon(eps, None, 0)
+        lat.set_force((1e-5, 0.0, 0.0))
+        lat.init_equilibrium()
+        st = lat.step(2)
+        rho = torch.empty(N, device="cuda", dtype=torch.float32)
+        u = torch.empty(3 * N, device="cuda", dtype=torch.float32)
+        lat.moments_into(rho=rho, u=u)
+        torch.cuda.synchronize()
+        out[kern] = (st, rho, u)
+        lat.close()
+    (sr, rr, ur), (sc, rc, uc) = out["row"], out["cell"]
+    assert not sr["nan_seen"] and not sc["nan_seen"]
+    assert abs(sr["mass"] - sc["mass"]) <= 1e-9 * abs(sc["mass"])
+    assert float((rr - rc).abs().max()) <= 1e-5
+    du = float(torch.linalg.vector_norm((ur - uc).double()))
+    assert float(uc.abs().max()) > 1e-6
+    assert du <= 1e-4 * float(torch.linalg.vector_norm(uc.double()))
