@@ -66,6 +66,13 @@ def test_params_default_and_device_bytes_need_no_gpu():
     assert 19 * n * 4 < b32 < 19 * n * 4 + 3 * n * 4 + (1 << 24)
     assert 19 * n * 2 < b16 < b32
     assert lbm.device_bytes("D2Q9", (4, 4, 2)) == 0  # invalid: D2Q9 needs nz = 1
+    # d_t phi is double-buffered like phi_ref (a refresh fills the spare pair):
+    # two pitched FP32 fields, rows of 45 cells stored at a pitch of 48
+    stored = 48 * 20 * 12
+    with_deps = lbm.device_bytes("D3Q19", (45, 20, 12), "fp32", with_deps=True)
+    assert with_deps - lbm.device_bytes("D3Q19", (45, 20, 12), "fp32") == 2 * stored * 4
+    with_deps64 = lbm.device_bytes("D3Q19", (45, 20, 12), "fp64", with_deps=True)
+    assert with_deps64 - lbm.device_bytes("D3Q19", (45, 20, 12), "fp64") == 2 * stored * 8
 
 
 def test_noalloc_limits_match_the_header():
