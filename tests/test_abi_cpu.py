@@ -84,3 +84,52 @@ def test_noalloc_limits_match_the_header():
     assert re.search(r"#define LBM_NOALLOC_MAX_CELLS \(\(long long\)\(LBM_NOALLOC_SCRATCH_BYTES / 20\)\)", text)
     assert lbm.NOALLOC_SCRATCH_BYTES == scratch
     assert lbm.NOALLOC_MAX_CELLS == scratch // 20
+
+
+def _params(**kw):
+    p = lbm.Params()
+    assert lbm.lib().lbm_vanse_params_default(ctypes.byref(p)) == 0
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+@pytest.mark.parametrize("kw,word", [
+    (dict(tau=0.5), "tau"), (dict(tau=float("nan")), "tau"), (dict(lattice=3), "lattice"),
+    (dict(storage=7), "storage"), (dict(nx=0), "nx"), (dict(lattice=0, nz=2), "D2Q9"),
+    (dict(quad_dim=4), "quad_dim"), (dict(rho0=0.0), "rho0"),
+    (dict(lattice=0, nz=1, walls=4), "walls"), (dict(quad_axes=8), "quad_axes")])
+def test_create_rejects_bad_parameters_on_the_host(kw, word):
+    """Parameter checks run before any device work: LBM_EINVAL, no handle,
+    and a message naming the parameter."""
+    p = _params(**kw)
+    h = ctypes.c_void_p()
+    assert lbm.lib().lbm_vanse_create(ctypes.byref(p), ctypes.byref(h)) == -1
+    assert h.value is None
+    assert word in lbm.last_error(None)
+
+
+def test_create_over_budget_fails_with_enomem_on_the_host():
+    """Admission by HBM budget (the serving path's failure mode), injected
+    with a budget far below the lattice's device bytes."""
+    p = _params(nx=64, ny=64, nz=64, hbm_budget_bytes=1 << 20)
+    h = ctypes.c_void_p()
+    assert lbm.lib().lbm_vanse_create(ctypes.byref(p), ctypes.byref(h)) == -2
+    assert h.value is None
+    assert "budget" in lbm.last_error(None)
+
+
+def test_null_handles_are_rejected_on_the_host():
+    L = lbm.lib()
+    assert L.lbm_vanse_set_epsilon(None, None, None, 0, 0) == -1
+    assert L.lbm_vanse_stage_epsilon(None, None, None, 0, 0) == -1
+    assert L.lbm_vanse_commit_epsilon(None) == -1
+    assert L.lbm_vanse_set_force(None, None, None, None, 0, 0) == -1
+    assert L.lbm_vanse_init_equilibrium(None, None, None, 0, 0) == -1
+    assert L.lbm_vanse_step(None, 1, 0.0, 0, None) == -1
+    assert L.lbm_vanse_moments(None, None, None, None, 0) == -1
+    assert L.lbm_vanse_get_populations(None, None) == -1
+    assert L.lbm_vanse_steps_done(None) == -1
+    assert L.lbm_vanse_batch_step(None, 1, 0) == -1
+    assert "NULL" in lbm.last_error(None)
+    L.lbm_vanse_destroy(None)  # accepted
