@@ -313,6 +313,26 @@ def test_invalid_inputs_are_rejected():
 
 # ------------------------------------------------------- row-staged kernel
 
+
+def test_nan_in_the_moments_is_reported_as_unstable():
+    """A check step that meets NaN in M0 or u returns LBM_EUNSTABLE and
+    names it (the state is left as it is).  The NaN comes in through a
+    device-side force field, which the library does not scan."""
+    import torch
+    nx, ny, nz = 32, 16, 8
+    n = nx * ny * nz
+    lat = lbm.Lattice("D3Q19", (nx, ny, nz), tau=0.6, storage="fp32")
+    lat.set_force((1e-6, 0.0, 0.0))
+    lat.init_equilibrium()
+    assert not lat.step(4)["nan_seen"]
+    f = torch.zeros(3 * n, device="cuda", dtype=torch.float32)
+    f[1000] = float("nan")
+    lat.set_force((1e-6, 0.0, 0.0), f)
+    with pytest.raises(lbm.LbmError) as ex:
+        lat.step(3)
+    assert ex.value.code == -4 and "NaN" in str(ex.value)
+    lat.close()
+
 def _row_pair(lattice, shape, storage, walls, tv, steps_chunks, refresh=True):
     nx, ny, nz = shape
     N = nx * ny * nz
