@@ -29,9 +29,9 @@ _LIB_PATH = os.path.join(_BUILD, "liblbm_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-LATTICES = {"D2Q9": 0, "D3Q19": 1, "D3Q27": 2}
-Q_OF = {0: 9, 1: 19, 2: 27}
-DIM_OF = {0: 2, 1: 3, 2: 3}
+LATTICES = {"D2Q9": 0, "D3Q19": 1, "D3Q27": 2, "D1Q3": 3}
+Q_OF = {0: 9, 1: 19, 2: 27, 3: 3}
+DIM_OF = {0: 2, 1: 3, 2: 3, 3: 1}
 
 
 def build(force: bool = False) -> str:
@@ -60,6 +60,9 @@ class _Problem(ctypes.Structure):
         ("g", ctypes.c_double * 3),
         ("force", ctypes.c_void_p), ("dforce_dt", ctypes.c_void_p),
         ("n_force", ctypes.c_longlong),
+        ("drag_model", ctypes.c_int),
+        ("drag_c1", ctypes.c_double), ("drag_c2", ctypes.c_double), ("drag_d", ctypes.c_double),
+        ("les_cs", ctypes.c_double),
     ]
 
 
@@ -121,6 +124,25 @@ def quad_weights(quad_dim: int):
     return w
 
 
+def quadrature_axes(eps_ref, deps_dt=None, dims=3):
+    """The quadrature rule Sec. 2.2 selects "by the number of directions in
+    which phi varies": (quad_axes, quad_dim) with bit a set when phi_ref (or
+    d_t phi) differs anywhere from its periodic neighbour along axis a < dims
+    (exact comparison), and every axis when phi is uniform.  Fields have
+    shape (nz, ny, nx)."""
+    mask = 0
+    for f in (eps_ref, deps_dt):
+        if f is None:
+            continue
+        f = np.asarray(f)
+        for a in range(dims):
+            if np.any(np.roll(f, -1, axis=2 - a) != f):
+                mask |= 1 << a
+    if mask == 0:
+        mask = (1 << dims) - 1
+    return mask, bin(mask).count("1")
+
+
 def cell_terms(lattice: int, M0: float, u, F, tau: float):
     """(f^eq[Q], Omega^F[Q]) of one cell (eq. (feq) and the Guo term)."""
     q = Q_OF[lattice]
@@ -143,7 +165,10 @@ class Problem:
 
     def __init__(self, lattice, nx, ny, nz=1, tau=0.8, rho0=1.0, quad_dim=None,
                  quad_axes=None, walls=0, eps_ref=None, deps_dt=None, n_eps=0,
-                 g=(0.0, 0.0, 0.0), force=None, dforce_dt=None, n_force=0):
+                 g=(0.0, 0.0, 0.0), force=None, dforce_dt=None, n_force=0, drag=None,
+                 les_cs=0.0):
+        """drag: None, or (c1, c2, d) of the Ergun-type drag law (R9 of
+        lbm_oracle.c); les_cs: Smagorinsky constant (R10), 0 = BGK."""
         if isinstance(lattice, str):
             lattice = LATTICES[lattice]
         self.lattice = lattice
@@ -159,6 +184,8 @@ class Problem:
             quad_dim = bin(quad_axes).count("1")
         self.quad_dim, self.quad_axes, self.walls = quad_dim, quad_axes, walls
         self.g = tuple(float(v) for v in (list(g) + [0.0] * 3)[:3])
+        self.drag = None if drag is None else tuple(float(v) for v in drag)
+        self.les_cs = float(les_cs)
         self.set_epsilon(np.ones(self.shape) if eps_ref is None else eps_ref, deps_dt, n_eps)
         self.set_force(self.g, force, dforce_dt, n_force)
 
@@ -187,6 +214,10 @@ class Problem:
         p.force = _ptr(self.force)
         p.dforce_dt = _ptr(self.dforce_dt)
         p.n_force = self.n_force
+        if self.drag is not None:
+            p.drag_model = 1
+            p.drag_c1, p.drag_c2, p.drag_d = self.drag
+        p.les_cs = self.les_cs
         return p
 
     def init(self, p0=None, u0=None, with_integral=False, half_force=False, n=0):

@@ -50,6 +50,21 @@
  *       interpretation the introduction attributes to the earlier scheme of
  *       Zhang et al., kept for the comparison of Sec. 1's claim that it
  *       misses the pressure.  Everything else is the same update.
+ *   R9  Phase-interaction drag (Sec. 2.2 lists drag among the forces F_k of
+ *       the force sum; the Conclusion names interaction forces as the next
+ *       step).  Ergun-type law of a fixed bed of particles of diameter d:
+ *       F_D = -(b_lin + b_q |u|) u, b_lin = rho~ c1 (1 - phi)^2 nu / (phi d^2),
+ *       b_q = rho~ c2 (1 - phi) / d (Ergun: c1 = 150, c2 = 1.75), phi and
+ *       rho~ of the cell at time n, nu = (tau - 1/2)/3.  It is taken
+ *       implicitly in eq. (velocity) (see orc_cell_macro), so u and the
+ *       force sum stay consistent with the Guo scheme.
+ *   R10 Smagorinsky large-eddy closure (the Conclusion names LES as a use of
+ *       the scheme): a local relaxation time from the non-equilibrium
+ *       momentum flux, tau_eff = (tau + sqrt(tau^2 + 18 sqrt(2) C^2 Q / M0))/2,
+ *       Q = |Pi^neq|, Pi^neq_ab = sum_i xi_ia xi_ib (f_i - f_i^eq): the root
+ *       of nu_eff = nu + (C Delta)^2 |S| with |S| = sqrt(2 S:S) from
+ *       S = -Pi^neq / (2 c_s^2 M0 tau_eff), Delta = 1.  The Guo term uses
+ *       1 - 1/(2 tau_eff).  C = 0 is the BGK update unchanged.
  *
  * Canonical evaluation order.  Every sum runs in ascending index order and
  * starts from 0.0; products are evaluated left to right as written below.
@@ -67,7 +82,8 @@
 
 /* ------------------------------------------------------------------------ */
 /* Velocity sets (Table "latt_par" for D2Q9, Table "latt_3d" for D3Q27;      */
-/* D3Q19 from the textbook the paper cites for the CE analysis).             */
+/* D3Q19 and D1Q3 from the textbook the paper cites for the CE analysis;     */
+/* Sec. 2.2 names one-dimensional stencils beside the 2D and 3D ones).       */
 /* ------------------------------------------------------------------------ */
 
 #define ORC_MAXQ 27
@@ -79,6 +95,8 @@ typedef struct {
   double w[ORC_MAXQ];    /* w_i */
   int opp[ORC_MAXQ];     /* index of -xi_i */
 } orc_vset;
+
+static const int ORC_D1Q3_C[3][3] = {{0, 0, 0}, {1, 0, 0}, {-1, 0, 0}};
 
 static const int ORC_D2Q9_C[9][3] = {
     {0, 0, 0},
@@ -119,6 +137,13 @@ static int orc_make_vset(int lattice, orc_vset *v) {
       for (a = 0; a < 3; ++a) v->c[i][a] = ORC_D3Q27_C[i][a];
       v->w[i] = (i == 0) ? 8.0 / 27.0
                          : (i <= 6 ? 2.0 / 27.0 : (i <= 18 ? 1.0 / 54.0 : 1.0 / 216.0));
+    }
+  } else if (lattice == 3) { /* D1Q3: one-dimensional stencil, textbook 2/3, 1/6 */
+    v->d = 1;
+    v->q = 3;
+    for (i = 0; i < 3; ++i) {
+      for (a = 0; a < 3; ++a) v->c[i][a] = ORC_D1Q3_C[i][a];
+      v->w[i] = (i == 0) ? 2.0 / 3.0 : 1.0 / 6.0;
     }
   } else {
     return -1;
@@ -163,6 +188,10 @@ typedef struct {
   const double *force;      /* optional field, 3*N component-major, or NULL */
   const double *dforce_dt;  /* its time derivative, or NULL */
   long long n_force;
+  int drag_model;           /* R9: 0 none, 1 Ergun-type drag */
+  double drag_c1, drag_c2;  /* R9: viscous and inertial coefficients */
+  double drag_d;            /* R9: particle diameter (lattice units) */
+  double les_cs;            /* R10: Smagorinsky constant, 0 = plain BGK */
 } orc_problem;
 
 static size_t orc_ncells(const orc_problem *P) {
@@ -201,6 +230,7 @@ static int orc_validate(const orc_problem *P, orc_vset *v) {
   if (orc_make_vset(P->lattice, v)) return -1;
   if (P->nx < 1 || P->ny < 1 || P->nz < 1) return -1;
   if (v->d == 2 && P->nz != 1) return -1;
+  if (v->d == 1 && (P->ny != 1 || P->nz != 1)) return -1;
   if (!(P->tau > 0.5)) return -1;
   if (!P->eps_ref) return -1;
   {
@@ -284,7 +314,40 @@ static void orc_cell_macro(const orc_problem *P, const orc_vset *v, long long n,
   }
 
   /* eq. (velocity): u = (sum xi f + dt/2 sum F) / sum f */
-  for (a = 0; a < 3; ++a) m->u[a] = (m->J[a] + 0.5 * m->F[a]) / m->M0;
+  if (!P->drag_model) {
+    for (a = 0; a < 3; ++a) m->u[a] = (m->J[a] + 0.5 * m->F[a]) / m->M0;
+    return;
+  }
+
+  /* R9: the phase-interaction drag F_D = -(b_lin + b_q |u|) u joins the
+     force sum, taken implicitly in eq. (velocity): with b = J + F/2 (every
+     other force) the velocity solves (M0 + (b_lin + b_q |u|)/2) u = b, so
+     |u| = s is the positive root of (b_q/2) s^2 + (M0 + b_lin/2) s - |b| = 0,
+     written without cancellation as s = 2|b| / (A + sqrt(A^2 + 2 b_q |b|)),
+     A = M0 + b_lin/2.  Then u = b / (A + b_q s/2) and F += F_D, so that
+     eq. (velocity) holds with the full force sum. */
+  {
+    double b[3], bn, e_x, one_m, nu, blin, bq, A, sp, den, fd;
+    e_x = e_c;
+    one_m = 1.0 - e_x;
+    nu = (P->tau - 0.5) / 3.0;
+    blin = m->rho * P->drag_c1 * one_m * one_m * nu / (e_x * P->drag_d * P->drag_d);
+    bq = m->rho * P->drag_c2 * one_m / P->drag_d;
+    bn = 0.0;
+    for (a = 0; a < 3; ++a) {
+      b[a] = m->J[a] + 0.5 * m->F[a];
+      bn = bn + b[a] * b[a];
+    }
+    bn = sqrt(bn);
+    A = m->M0 + 0.5 * blin;
+    sp = 2.0 * bn / (A + sqrt(A * A + 2.0 * bq * bn));
+    den = A + 0.5 * bq * sp;
+    for (a = 0; a < 3; ++a) {
+      m->u[a] = b[a] / den;
+      fd = (blin + bq * sp) * m->u[a];
+      m->F[a] = (a < v->d) ? m->F[a] - fd : 0.0;
+    }
+  }
 }
 
 /* eq. (feq) with the zeroth moment M0 in place of rho~ phi:
@@ -437,13 +500,33 @@ int oracle_step(const orc_problem *P, long long n, const double *f, double *fnew
         orc_macro m;
         double usq, uF;
         if (orc_is_solid(P, x, y, z)) continue;
+        double om = omega, cfl = cf;
         orc_cell_macro(P, &v, n, x, y, z, fc, &m);
         usq = m.u[0] * m.u[0] + m.u[1] * m.u[1] + m.u[2] * m.u[2];
         uF = m.u[0] * m.F[0] + m.u[1] * m.F[1] + m.u[2] * m.F[2];
+        if (P->les_cs > 0.0) {
+          /* R10: Pi^neq_ab = sum_i xi_ia xi_ib (f_i - f_i^eq), Q = |Pi^neq| */
+          double pi[3][3], Q2 = 0.0, teff;
+          int a, b;
+          for (a = 0; a < 3; ++a)
+            for (b = 0; b < 3; ++b) pi[a][b] = 0.0;
+          for (i = 0; i < v.q; ++i) {
+            double fneq = fc[i] - orc_feq(&v, i, m.M0, m.u, usq);
+            for (a = 0; a < 3; ++a)
+              for (b = 0; b < 3; ++b)
+                pi[a][b] = pi[a][b] + (double)v.c[i][a] * (double)v.c[i][b] * fneq;
+          }
+          for (a = 0; a < 3; ++a)
+            for (b = 0; b < 3; ++b) Q2 = Q2 + pi[a][b] * pi[a][b];
+          teff = 0.5 * (P->tau + sqrt(P->tau * P->tau +
+                                      18.0 * sqrt(2.0) * P->les_cs * P->les_cs * sqrt(Q2) / m.M0));
+          om = 1.0 / teff;
+          cfl = 1.0 - 0.5 / teff;
+        }
         for (i = 0; i < v.q; ++i) {
           double feq = orc_feq(&v, i, m.M0, m.u, usq);
-          double S = orc_guo(&v, i, cf, m.u, m.F, uF);
-          double fstar = fc[i] + omega * (feq - fc[i]) + S;
+          double S = orc_guo(&v, i, cfl, m.u, m.F, uF);
+          double fstar = fc[i] + om * (feq - fc[i]) + S;
           int xn = orc_wrap(x + v.c[i][0], P->nx);
           int yn = orc_wrap(y + v.c[i][1], P->ny);
           int zn = orc_wrap(z + v.c[i][2], P->nz);

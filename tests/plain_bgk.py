@@ -16,6 +16,7 @@ import itertools
 import numpy as np
 
 GROUP_WEIGHTS = {
+    "D1Q3": (1, {0: 2 / 3, 1: 1 / 6}),
     "D2Q9": (2, {0: 4 / 9, 1: 1 / 9, 2: 1 / 36}),
     "D3Q19": (3, {0: 1 / 3, 1: 1 / 18, 2: 1 / 36}),
     "D3Q27": (3, {0: 8 / 27, 1: 2 / 27, 2: 1 / 54, 3: 1 / 216}),

@@ -34,8 +34,8 @@ def _golden_eoc():
     raise AssertionError("eoc missing from golden file")
 
 
-def run_mms(example, N, t_end, lattice=None, chunk=4000, quad_dim=None):
-    m = I.MMS(example, N)
+def run_mms(example, N, t_end, lattice=None, chunk=4000, quad_dim=None, tau=None):
+    m = I.MMS(example, N, tau=tau)
     lat = lattice or m.lattice
     f0 = m.lattice_fields(0)
     nz, ny, nx = m.shape
@@ -158,3 +158,69 @@ def test_pointwise_density_misses_the_pressure():
         assert abs(v) < 0.5, ("p", norm, v)
     _, epc = run_mms(1, 32, 15.0)
     assert ep2["L2"] > 100 * epc["L2"]
+
+
+def test_stationary_3d_example_converges_second_order():
+    """Example 2 (stationary, three-dimensional) on D3Q27 with D3Q7
+    quadrature at the paper's tau = 0.53, N = 16 -> 32, error taken at
+    t = 3 s (three e-folding times of the slowest viscous mode, 1/(nu pi^2)):
+    the only stationary 3D case of Sec. 3, and the one that exercises the
+    D3Q7 rule against a closed form.  L1 and L2 orders of u and every order of
+    p are two within 0.1 (the Linf order of u reaches 2.12 at this
+    resolution; the GPU test checks it at N = 32 -> 64)."""
+    target = _golden_eoc()
+    eu1, ep1 = run_mms(2, 16, 3.0)
+    eu2, ep2 = run_mms(2, 32, 3.0)
+    eu, ep = _eoc(eu1, eu2), _eoc(ep1, ep2)
+    for norm in ("L1", "L2"):
+        assert abs(eu[norm] - target) < EOC_TOL, ("u", norm, eu[norm])
+    for norm, v in ep.items():
+        assert abs(v - target) < EOC_TOL, ("p", norm, v)
+
+
+def test_transient_2d_example_converges_second_order():
+    """Example 4 (transient, two-dimensional) on D2Q9 with D2Q5 quadrature,
+    N = 16 -> 32, exact phi and force every step, error at t = 2 s.  With
+    phi down to 0.1 the velocity u = 0.5 + 1/phi reaches 10.5 m/s; at the
+    paper's tau = 0.5075 the BGK scheme is unstable below N = 64 on this
+    field (measured: the pressure error grows to 4e2 at N = 32), so the
+    oracle pin takes tau = 0.52 (diffusive scaling, nu_L = 0.00667), where
+    N = 16 -> 32 is stable.  L1 and L2 orders of u and every order of p are
+    two within 0.1 (the Linf order of u, 1.87 here, is checked on the GPU at
+    finer resolution)."""
+    target = _golden_eoc()
+    eu1, ep1 = run_mms(4, 16, 2.0, tau=0.52)
+    eu2, ep2 = run_mms(4, 32, 2.0, tau=0.52)
+    eu, ep = _eoc(eu1, eu2), _eoc(ep1, ep2)
+    for norm in ("L1", "L2"):
+        assert abs(eu[norm] - target) < EOC_TOL, ("u", norm, eu[norm])
+    for norm, v in ep.items():
+        assert abs(v - target) < EOC_TOL, ("p", norm, v)
+
+
+def test_transient_1d_example_on_the_d1q3_lattice():
+    """Example 3 on the one-dimensional D1Q3 lattice (D1Q3 quadrature, tau =
+    0.5075), N = 32 -> 64, exact phi and force every step: every norm of u
+    and p at order two within 0.1, as on the N x 1 D2Q9 lattice."""
+    target = _golden_eoc()
+    eu1, ep1 = run_mms(3, 32, 12.0, lattice="D1Q3")
+    eu2, ep2 = run_mms(3, 64, 12.0, lattice="D1Q3")
+    for name, e in (("u", _eoc(eu1, eu2)), ("p", _eoc(ep1, ep2))):
+        for norm, v in e.items():
+            assert abs(v - target) < EOC_TOL, (name, norm, v)
+
+
+def test_quadrature_axes_follow_the_variation_of_phi():
+    """Sec. 2.2 picks D1Q3, D2Q5 or D3Q7 by the number of directions in which
+    phi varies: a field varying along x only gives the D1Q3 rule on x, one
+    varying in x and z the D2Q5 rule on (x, z), the porous field all three
+    axes, a uniform field every axis (where every rule gives phi)."""
+    nz, ny, nx = 6, 5, 8
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    assert oracle.quadrature_axes(0.5 + 0.1 * np.sin(x)) == (1, 1)
+    assert oracle.quadrature_axes(0.5 + 0.1 * np.sin(x + 2 * z)) == (5, 2)
+    assert oracle.quadrature_axes(np.full((nz, ny, nx), 0.7)) == (7, 3)
+    assert oracle.quadrature_axes(np.full((nz, ny, nx), 0.7), 0.01 * np.cos(y)) == (2, 1)
+    e = I.eps_random_spheres((nz, 12, 16), seed_offset=3, rmin=2, rmax=3, sigma=1.0)
+    assert oracle.quadrature_axes(e) == (7, 3)
+    assert oracle.quadrature_axes(np.full((1, ny, nx), 0.7), dims=2) == (3, 2)
