@@ -86,53 +86,116 @@ def kernel_source_hash() -> str:
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle sampling during the timed region."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    """SM clock and clock-event reasons sampled DURING a timed region.
 
-    def __init__(self, gpu_index: int):
+    Reads NVML directly (libnvidia-ml through ctypes, every 2 ms, so that a
+    timed region of a few milliseconds still gets samples); falls back to
+    ``nvidia-smi -lms 20`` where NVML cannot be loaded.  Reads only: it
+    changes no setting of the GPU."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+    SMI_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, interval_s: float = 0.002):
         self.gpu = gpu_index
-        self.samples = []
+        self.interval = interval_s
+        self.samples = []      # (sm_mhz, max_mhz, reason names)
         self.proc = None
+        self.thread = None
+        self.stop = threading.Event()
+        self.source = None
+
+    def _nvml(self):
+        import ctypes
+        for name in ("libnvidia-ml.so.1", "libnvidia-ml.so"):
+            try:
+                lib = ctypes.CDLL(name)
+                break
+            except OSError:
+                lib = None
+        if lib is None or lib.nvmlInit_v2() != 0:
+            return None
+        dev = ctypes.c_void_p()
+        handle = None
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(self.gpu).uuid)
+            key = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+            if lib.nvmlDeviceGetHandleByUUID(key.encode(), ctypes.byref(dev)) == 0:
+                handle = dev
+        except Exception:
+            handle = None
+        if handle is None:
+            if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.gpu), ctypes.byref(dev)) != 0:
+                return None
+            handle = dev
+        reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        return lib, handle, reasons_fn
+
+    def _poll_nvml(self, lib, handle, reasons_fn):
+        import ctypes
+        clk, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self.stop.is_set():
+            if (lib.nvmlDeviceGetClockInfo(handle, 1, ctypes.byref(clk)) == 0
+                    and lib.nvmlDeviceGetMaxClockInfo(handle, 1, ctypes.byref(mx)) == 0
+                    and reasons_fn(handle, ctypes.byref(rs)) == 0):
+                names = [v for k, v in self.REASONS.items() if rs.value & k]
+                self.samples.append((float(clk.value), float(mx.value), names))
+            self.stop.wait(self.interval)
+
+    def _read_smi(self):
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.proc.stdout:
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 9 and p[1].replace(".", "").isdigit() and p[2].replace(".", "").isdigit():
+                self.samples.append((float(p[1]), float(p[2]),
+                                     [names[j] for j in range(4) if p[5 + j].lower() == "active"]))
 
     def __enter__(self):
+        nv = None
+        try:
+            nv = self._nvml()
+        except Exception:
+            nv = None
+        if nv is not None:
+            self.source = "nvml"
+            self.thread = threading.Thread(target=self._poll_nvml, args=nv, daemon=True)
+            self.thread.start()
+            return self
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.SMI_Q}",
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.source = "nvidia-smi"
+            self.thread = threading.Thread(target=self._read_smi, daemon=True)
             self.thread.start()
         except Exception:
             self.proc = None
         return self
 
-    def _read(self):
-        for line in self.proc.stdout:
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) >= 9:
-                self.samples.append(parts)
-
     def __exit__(self, *exc):
+        self.stop.set()
         if self.proc:
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
 
     def summary(self):
         if not self.samples:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
-        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
-        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[j] for s in self.samples for j in range(4)
-                          if s[5 + j].lower() == "active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(self.samples)}
+        sm = [s[0] for s in self.samples]
+        mx = [s[1] for s in self.samples]
+        reasons = sorted({r for s in self.samples for r in s[2]})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": reasons,
+                "samples": len(self.samples), "source": self.source}
 
 
 def eps_fields(L, t):
@@ -217,6 +280,15 @@ def run_gpu(args, rank, world):
         return ev
 
     results = {}
+    tuning = {}
+    if args.tune:
+        # a bounded sweep of the row kernel's launch shapes on this lattice
+        # (cached per size bucket; the lattices below read the cache)
+        from paper_2208_09267_gb300 import tune
+        for storage in args.storages:
+            best, ms = tune.tune_step("D3Q19", storage, (L, L, L), tau=TAU, steps=10, warmup=3,
+                                      blocks=[(256, 1)])
+            tuning[storage] = {"best": best, "ms_per_step": ms}
     for storage in args.storages:
         lat = make(storage)
         device_run(lat, args.warmup, False)
@@ -243,7 +315,8 @@ def run_gpu(args, rank, world):
         kname = "step_row_kernel" if lat.row_kernel else "step_fast_kernel"
         results[storage] = {"total_ms": total_ms, "kernel_ms": step_ms / nk, "launches": launches,
                             "clocks": clk.summary(), "mass": st["mass"],
-                            "kernel": f"{kname}<D3Q19,{'float' if storage == 'fp32' else '__half'}>"}
+                            "kernel": f"{kname}<D3Q19,{'float' if storage == 'fp32' else '__half'}>",
+                            "launch_shape": lat.launch_shape, "tuned_from": lat.tuned_from}
         lat.close()
 
     # end to end through the C ABI with host buffers (FP32).  The refreshes
@@ -319,7 +392,7 @@ def run_gpu(args, rank, world):
                        "stream during the 10 steps before it and committed after them; each "
                        "10-step call reads its check statistics back"}
         lat.close()
-    return results, e2e
+    return results, e2e, tuning
 
 
 def run_porous(steps=200, warmup=10, shape=(512, 256, 256), storages=("fp32", "fp16")):
@@ -366,18 +439,29 @@ def run_porous(steps=200, warmup=10, shape=(512, 256, 256), storages=("fp32", "f
     return out
 
 
-def run_batched(count=256, steps=200, storages=("fp16", "fp32")):
-    """Many independent lattices (half D2Q9 squares of side 32..512, half
-    D3Q19 cubes of side 32..128, product-sine phi, tau in [0.55, 1.2]) advanced
-    together by the batched graph-captured kernels, against the plain
-    per-lattice FP32 path (one handle per lattice, stepped one after the
-    other).  Returns GLUPS and lattices solved per second for each."""
+def batch_bytes(specs, storage):
+    """Algorithmic bytes of one step of every lattice of a batch: per cell one
+    read and one write of each population plus phi_ref (static phi)."""
+    b = {"fp32": 4, "fp16": 2}[storage]
+    q = {"D2Q9": 9, "D3Q19": 19, "D3Q27": 27}
+    return sum(s.cells * (2 * q[s.lattice] * b + 4) for s in specs)
+
+
+def run_batched(count=256, steps=1000, storages=("fp16", "fp32")):
+    """The batched workload: 256 independent lattices (half D2Q9 squares of
+    side 32..512, half D3Q19 cubes of side 32..128, product-sine phi, tau in
+    [0.55, 1.2]), 1000 steps each, advanced together by the batched
+    graph-captured kernels, against the plain per-lattice FP32 path (one
+    handle per lattice, stepped one after the other).  Returns GLUPS,
+    lattices solved per second and, for the batched legs, the aggregate
+    fraction of the copy bandwidth (algorithmic bytes of every member)."""
     import torch
 
     from paper_2208_09267_gb300 import inputs, lbm
     specs = inputs.batch_specs(count=count, steps=steps)
     cells = sum(s.cells for s in specs)
     stream = torch.cuda.current_stream().cuda_stream
+    peak, peak_kind = peak_hbm()
     out = {"lattices": count, "steps": steps, "cells": cells}
 
     def make(storage, s):
@@ -391,7 +475,7 @@ def run_batched(count=256, steps=200, storages=("fp16", "fp32")):
     for storage in storages:
         lats = [make(storage, s) for s in specs]
         b = lbm.Batch(max_members=count, max_tiles=sum((lt.stored + 4095) // 4096 for lt in lats) + 8,
-                      stream=stream)
+                      stream=stream, storage=storage)
         # replays of k steps (their graph is captured in the warm-up replay)
         k = 100 if steps % 100 == 0 else (50 if steps % 50 == 0 else 10)
         for lt in lats:
@@ -406,8 +490,11 @@ def run_batched(count=256, steps=200, storages=("fp16", "fp32")):
         b.close()
         for lt in lats:
             lt.close()
+        gbs = batch_bytes(specs, storage) * steps / dt / 1e9
         out[f"batched_{storage}"] = {"glups": cells * steps / dt / 1e9, "solves_per_s": count / dt,
-                                     "seconds": dt}
+                                     "seconds": dt, "achieved_gbs": gbs, "frac": gbs / peak,
+                                     "peak_kind": f"{peak_kind} copy bandwidth",
+                                     "tile_cells_tuned_from": b.tuned_from}
     # plain per-lattice FP32: one solver per lattice, each stepped alone
     lats = [make("fp32", s) for s in specs]
     for lt in lats:
@@ -420,64 +507,121 @@ def run_batched(count=256, steps=200, storages=("fp16", "fp32")):
     dt = time.perf_counter() - t
     for lt in lats:
         lt.close()
+    gbs = batch_bytes(specs, "fp32") * steps / dt / 1e9
     out["per_lattice_fp32"] = {"glups": cells * steps / dt / 1e9, "solves_per_s": count / dt,
-                               "seconds": dt}
+                               "seconds": dt, "achieved_gbs": gbs, "frac": gbs / peak}
     return out
 
 
-def run_serving(rate=100.0, count=48, sides=(32, 96), steps=(500, 4000)):
-    """Poisson arrivals of D3Q19 solves (side log-uniform, random-sphere or
-    sine phi, step budget log-uniform or residual 1e-8 with that cap) served
-    with continuous batching in FP16-shifted storage, against plain
-    per-request FP32 (sequential).  Reports solves/s and p50/p99 latency."""
+def run_serving(rates=(10.0, 100.0, 500.0), window_s=6.0, max_requests=20,
+                sides=(32, 192), steps=(500, 20000)):
+    """The served workload: for each arrival rate, a Poisson stream of D3Q19
+    solves (side log-uniform in `sides`, random-sphere or sine phi 50/50, a
+    step budget log-uniform in `steps`, half of them with a steady-state
+    residual target of 1e-8 capped by that budget), admitted by an 80 GB HBM
+    budget and served with continuous batching in FP16-shifted storage,
+    against plain per-request FP32 (one solver per request, sequential).
+    Each rate runs a bounded trace: the requests arriving within `window_s`
+    seconds, at most `max_requests` (the same problems at every rate), and
+    each arm stops at 3 * window_s; the line states how many completed.  Reports solves/s and
+    p50/p99 latency (arrival to result on the host) per rate, and for the
+    requests both completed with the same step count the relative L2
+    distance of the FP16 answer to the FP32 one."""
     import torch
 
     from paper_2208_09267_gb300 import serve
     stream = torch.cuda.current_stream().cuda_stream
-    reqs = serve.make_requests(rate, count, sides=sides, steps=steps)
-    srv = serve.Server(storage="fp16", hbm_budget=80e9, macro_steps=100, stream=stream,
-                       keep_results=True)
-    served = srv.run(reqs)
-    srv.close()
-    seq_reqs = [serve.Request(r.rid, r.spec, r.arrival, r.eps) for r in reqs]
-    seq = serve.run_sequential(seq_reqs, storage="fp32", check_every=100, stream=stream)
-    errs = []
-    for a, b in zip(reqs, seq_reqs):
-        if a.result is not None and b.result is not None and a.steps_done == b.steps_done:
-            ua, ub = a.result["u"].astype(np.float64), b.result["u"].astype(np.float64)
-            nb = np.linalg.norm(ub)
-            if nb > 0:
-                errs.append(float(np.linalg.norm(ua - ub) / nb))
-    return {"trace": f"Poisson {rate:g}/s, {count} requests, side log-uniform {sides}, steps "
-                     f"log-uniform {steps} (half with residual 1e-8), 80 GB budget",
-            "served_fp16": served, "sequential_fp32": seq,
-            "fp16_vs_fp32_u_rel_l2_max": max(errs) if errs else None,
-            "fp16_vs_fp32_compared": len(errs)}
+    out = {"trace": f"Poisson arrivals, D3Q19 side log-uniform {sides}, steps log-uniform {steps}, "
+                    f"half with residual 1e-8, spheres or sine phi 50/50, 80 GB budget, window "
+                    f"{window_s:g} s per rate (run capped at {3 * window_s:g} s)", "rates": {}}
+    for rate in rates:
+        count = int(min(max_requests, max(4, rate * window_s)))
+        # the same problems at every rate (their phi generated once, by the
+        # client, before the run)
+        reqs = serve.make_requests(rate, count, sides=sides, steps=steps, seed_offset=5000)
+        srv = serve.Server(storage="fp16", hbm_budget=80e9, macro_steps=100, stream=stream,
+                           keep_results=True)
+        served = srv.run(reqs, timeout_s=3 * window_s)
+        srv.close()
+        seq_reqs = [serve.Request(r.rid, r.spec, r.arrival, r.eps) for r in reqs]
+        seq = serve.run_sequential(seq_reqs, storage="fp32", check_every=100, stream=stream,
+                                   timeout_s=3 * window_s)
+        errs = []
+        for a, b in zip(reqs, seq_reqs):
+            if a.result is not None and b.result is not None and a.steps_done == b.steps_done:
+                ua, ub = a.result["u"].astype(np.float64), b.result["u"].astype(np.float64)
+                nb = np.linalg.norm(ub)
+                if nb > 0:
+                    errs.append((float(np.linalg.norm(ua - ub) / nb), a.status))
+        out["rates"][f"{rate:g}"] = {
+            "requests": count, "served_fp16": served, "sequential_fp32": seq,
+            "fp16_vs_fp32_u_rel_l2_max": max(e for e, _ in errs) if errs else None,
+            "fp16_vs_fp32_compared": len(errs),
+            "fp16_vs_fp32_compared_converged": sum(1 for _, st in errs if st == "converged")}
+    return out
 
 
-def cpu_baseline(sample_L=48, steps=None, budget_s=20.0):
-    """The FP64 oracle on the host cores, timed on a bounded sample of the
-    same workload (a sample_L^3 lattice with the same phi recipe)."""
+def _oracle_rate(P, f, steps, threads):
+    """GLUPS of `steps` oracle steps on `threads` host threads (0 = all)."""
     import oracle
+    oracle.set_threads(threads)
+    t = time.perf_counter()
+    P.run(f, 0, steps)
+    dt = time.perf_counter() - t
+    return P.n * steps / dt / 1e9, dt
+
+
+def cpu_baseline(sample_L=48, steps=None, budget_s=15.0, plan=True):
+    """The FP64 oracle on the host cores, timed on a bounded sample of the
+    same workload (a sample_L^3 lattice with the same phi recipe, all cores),
+    and with `plan`, bounded samples of the other workloads: the 64^2 D2Q9
+    case run in full on one thread, the D3Q19 sample on one thread, a
+    D3Q27 porous-channel block (64 x 32 x 32, walls on y) and eight lattices
+    of the batched workload (a few steps each), all cores."""
+    import oracle
+    from paper_2208_09267_gb300 import inputs
     oracle.build()
-    oracle.set_threads(0)
+    cores = os.cpu_count() or 1
     e, d = eps_fields(sample_L, 0)
-    P = oracle.Problem("D3Q19", sample_L, sample_L, sample_L, tau=TAU, eps_ref=e, deps_dt=d,
-                       g=G)
+    P = oracle.Problem("D3Q19", sample_L, sample_L, sample_L, tau=TAU, eps_ref=e, deps_dt=d, g=G)
     f = P.init()
+    oracle.set_threads(0)
     t = time.perf_counter()
     f = P.run(f, 0, 2)
     per = (time.perf_counter() - t) / 2
     if steps is None:
         steps = max(2, int(budget_s / max(per, 1e-6)))
-    t = time.perf_counter()
-    P.run(f, 2, steps)
-    dt = time.perf_counter() - t
-    cores = os.cpu_count() or 1
-    return {"value": sample_L ** 3 * steps / dt / 1e9, "unit": "GLUPS", "cores": cores,
-            "kind": "oracle",
-            "sample": f"D3Q19 {sample_L}^3 lattice, same phi recipe and tau, {steps} steps, "
-                      f"FP64 oracle with {cores} OpenMP threads ({dt:.1f} s)"}
+    value, dt = _oracle_rate(P, f, steps, 0)
+    out = {"value": value, "unit": "GLUPS", "cores": cores, "kind": "oracle",
+           "sample": f"D3Q19 {sample_L}^3 lattice, same phi recipe and tau, {steps} steps, "
+                     f"FP64 oracle with {cores} OpenMP threads ({dt:.1f} s)"}
+    if not plan:
+        return out
+    legs = {}
+    # the 64^2 D2Q9 FP64 case, all 1000 steps, one thread
+    e1 = inputs.eps_static_sine(64)
+    P1 = oracle.Problem("D2Q9", 64, 64, 1, tau=0.8, eps_ref=e1, g=(1e-6, 0, 0))
+    legs["d2q9_64x64_1000_steps_1_thread"] = _oracle_rate(P1, P1.init(), 1000, 1)[0]
+    # the space-time varying D3Q19 sample on one thread, 10 steps
+    legs[f"d3q19_{sample_L}^3_1_thread"] = _oracle_rate(P, f, 10, 1)[0]
+    # a block of the porous channel: D3Q27, walls on y, static phi
+    shape = (32, 32, 64)
+    e3 = inputs.eps_random_spheres(shape, seed_offset=2, wall_axis=1)
+    P3 = oracle.Problem("D3Q27", 64, 32, 32, tau=0.6, walls=2, eps_ref=e3, g=G)
+    legs["d3q27_porous_64x32x32_all_cores"] = _oracle_rate(P3, P3.init(), 20, 0)[0]
+    # eight lattices of the batched workload, 5 steps each, all cores
+    specs = inputs.batch_specs(count=256)[::32]
+    cells, secs = 0, 0.0
+    for sp in specs:
+        nz, ny, nx = sp.shape
+        Pb = oracle.Problem(sp.lattice, nx, ny, nz, tau=sp.tau, eps_ref=sp.eps(), g=sp.g)
+        _, dtb = _oracle_rate(Pb, Pb.init(), 5, 0)
+        cells += sp.cells * 5
+        secs += dtb
+    legs["batched_8_lattices_all_cores"] = cells / secs / 1e9
+    out["plan_glups"] = legs
+    oracle.set_threads(0)
+    return out
 
 
 def main():
@@ -490,15 +634,17 @@ def main():
     ap.add_argument("--block", type=int, nargs=2, default=[0, 0])
     ap.add_argument("--storages", nargs="+", default=["fp32", "fp16"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", dest="tune", action="store_false",
+                    help="skip the launch-shape sweep before the timed legs")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-porous", action="store_true")
     ap.add_argument("--porous-steps", type=int, default=200)
     ap.add_argument("--batch-count", type=int, default=256)
-    ap.add_argument("--batch-steps", type=int, default=200)
-    ap.add_argument("--serve-count", type=int, default=48)
-    ap.add_argument("--serve-rate", type=float, default=100.0)
+    ap.add_argument("--batch-steps", type=int, default=1000)
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[10.0, 100.0, 500.0])
+    ap.add_argument("--serve-window", type=float, default=6.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -515,7 +661,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        cb = cpu_baseline(sample_L=48 if L >= 48 else L, budget_s=max(5.0, args.steps * 0.5))
+        cb = cpu_baseline(sample_L=48 if L >= 48 else L, budget_s=max(5.0, args.steps * 0.5), plan=False)
         line = {"impl": "reference", "metric": metric_name(args.size), "value": cb["value"], "unit": "GLUPS",
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -529,7 +675,7 @@ def main():
         import torch
         torch.distributed.init_process_group("nccl")
 
-    res, e2e = run_gpu(args, rank, world)
+    res, e2e, tuning = run_gpu(args, rank, world)
     main_st = args.storages[0]
     r = res[main_st]
     glups = aggregate_glups(N, args.steps, r["total_ms"], world)
@@ -547,7 +693,8 @@ def main():
                      "frac": achieved / peak, "peak_kind": f"{peak_kind} copy bandwidth",
                      "traffic": profiled_traffic(main_st, src_hash),
                      "algorithmic_bytes_per_cell": bpc,
-                     "kernel": r["kernel"], "kernel_ms": r["kernel_ms"]},
+                     "kernel": r["kernel"], "kernel_ms": r["kernel_ms"],
+                     "launch_shape": r["launch_shape"], "tuned_from": r["tuned_from"]},
         "gpu_launches": r["launches"], "clocks": r["clocks"], "e2e": e2e,
     }
     for st, rr in res.items():
@@ -558,13 +705,16 @@ def main():
         line[st] = {"value": N / (rr["total_ms"] / args.steps) / 1e6, "unit": "GLUPS",
                     "kernel_ms": rr["kernel_ms"], "algorithmic_bytes_per_cell": bb,
                     "achieved_gbs": ach, "frac": ach / peak, "gpu_launches": rr["launches"],
-                    "traffic": profiled_traffic(st, src_hash), "clocks": rr["clocks"]}
+                    "traffic": profiled_traffic(st, src_hash), "clocks": rr["clocks"],
+                    "launch_shape": rr["launch_shape"], "tuned_from": rr["tuned_from"]}
+    if tuning:
+        line["tuning"] = tuning
     if rank == 0 and not args.no_batch:
         line["batched"] = run_batched(args.batch_count, args.batch_steps)
     if rank == 0 and not args.no_porous:
         line["porous_channel"] = run_porous(args.porous_steps)
     if rank == 0 and not args.no_serve:
-        line["serving"] = run_serving(args.serve_rate, args.serve_count)
+        line["serving"] = run_serving(tuple(args.serve_rates), args.serve_window)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(sample_L=48 if L >= 48 else L, budget_s=15.0)
     if rank == 0:

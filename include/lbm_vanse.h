@@ -53,8 +53,11 @@ typedef struct lbm_vanse *lbm_vanse_t;
 typedef struct lbm_vanse_batch *lbm_vanse_batch_t;
 
 /* Discrete velocity sets: D2Q9 (Table "latt_par"), D3Q27 (Table "latt_3d"),
-   D3Q19 (not in the paper; standard textbook weights 1/3, 1/18, 1/36). */
-enum lbm_lattice { LBM_D2Q9 = 0, LBM_D3Q19 = 1, LBM_D3Q27 = 2 };
+   D3Q19 (not in the paper; standard textbook weights 1/3, 1/18, 1/36), and
+   D1Q3 for one-dimensional problems (Sec. 2.2 names one-dimensional
+   stencils beside the 2D and 3D ones; textbook weights 2/3, 1/6; needs
+   ny = nz = 1 and is stepped one cell per thread). */
+enum lbm_lattice { LBM_D2Q9 = 0, LBM_D3Q19 = 1, LBM_D3Q27 = 2, LBM_D1Q3 = 3 };
 
 /* Population storage.  LBM_FP64: f_i stored and collided in double, in the
    canonical evaluation order, bit-identical to the FP64 reference.
@@ -83,7 +86,8 @@ enum { LBM_AXIS_X = 1u, LBM_AXIS_Y = 2u, LBM_AXIS_Z = 4u };
 typedef struct {
   int lattice;              /* enum lbm_lattice */
   int storage;              /* enum lbm_storage */
-  int nx, ny, nz;           /* cells per axis, >= 1; nz must be 1 for D2Q9 */
+  int nx, ny, nz;           /* cells per axis, >= 1; nz must be 1 for D2Q9,
+                               ny = nz = 1 for D1Q3 */
   double tau;               /* BGK relaxation time, eq. (lbe); > 0.5 */
   double rho0;              /* reference density; p = c_s^2 (rho~ - rho0) */
   int quad_dim;             /* row of Table "weights" (1, 2, 3); 0 = number
@@ -114,6 +118,44 @@ typedef struct {
                                rounding (unbiased; random bits from a
                                counter-based hash of cell and step, so runs
                                are reproducible), 1 = round to nearest */
+  int quad_auto;            /* 1 = choose the quadrature rule from phi (Sec.
+                               2.2: D1Q3, D2Q5 or D3Q7 "by the number of
+                               directions in which phi varies"): every
+                               set_epsilon / commit_epsilon scans phi_ref and
+                               d_t phi on the device and sets quad_axes to the
+                               axes along which a value differs from its
+                               neighbour's (every lattice axis when phi is
+                               uniform) and quad_dim to their number; the scan
+                               synchronises the handle's stream.  0 = use
+                               quad_axes and quad_dim as given. */
+  int drag_model;           /* phase-interaction drag in the force sum (Sec.
+                               2.2 lists drag among the forces F_k; the
+                               Conclusion names interaction forces):
+                               0 = none; 1 = Ergun-type law of a fixed bed of
+                               particles, F_D = -(b_lin + b_q |u|) u with
+                               b_lin = rho~ c1 (1 - phi)^2 nu / (phi d^2),
+                               b_q = rho~ c2 (1 - phi) / d, taken implicitly
+                               in eq. (velocity) (u and the force sum stay
+                               consistent with the Guo scheme).  Needs
+                               0 < phi <= 1 everywhere (phi = 1: no drag). */
+  double drag_c1, drag_c2;  /* Ergun coefficients (150 and 1.75 in Ergun's
+                               correlation), >= 0 */
+  double drag_d;            /* particle diameter, lattice units, > 0 */
+  double les_cs;            /* Smagorinsky constant C >= 0 (the Conclusion
+                               names LES): tau is replaced per cell by
+                               (tau + sqrt(tau^2 + 18 sqrt(2) C^2 |Pi^neq| /
+                               M0)) / 2, Pi^neq the non-equilibrium momentum
+                               flux, filter width one cell; 0 = BGK.
+                               drag_model or les_cs > 0 select the
+                               one-cell-per-thread kernel (kernel = 2 then
+                               fails with LBM_EINVAL). */
+  int row_consumers;        /* row-staged kernel: consumer warps per block
+                               (0 = the compiled default; values above the
+                               compiled maximum fall back to it) */
+  int row_stages;           /* row-staged kernel: rows staged in flight per
+                               block (0 = default; 2 .. compiled maximum).
+                               Neither changes the arithmetic, only the
+                               launch shape; the autotuner picks them. */
 } lbm_vanse_params;
 
 /* Global sums of the state at time n (pre-collision), taken on a check step
@@ -268,7 +310,11 @@ LBM_API int lbm_vanse_moments_f64(lbm_vanse_t h, double *rho, double *p, double 
    after the copies to the host have completed.  The first call on a device
    looks up the array's address there (cudaGetSymbolAddress, with that device
    current); when that set-up happens in the first call, make that call
-   before any stream capture begins.  rho, p: N values; u: 3*N values; any
+   before any stream capture begins.  The address is kept for the rest of
+   the process: it assumes that the device's primary context lives as long
+   as the process (a cudaDeviceReset, or a primary context torn down and
+   created again, leaves a stale address: do not call this entry point
+   after either).  rho, p: N values; u: 3*N values; any
    may be NULL.  Errors: LBM_EINVAL (NULL handle, lattice too large),
    LBM_ECUDA. */
 #define LBM_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
@@ -294,6 +340,13 @@ LBM_API int lbm_vanse_set_wait_limit(lbm_vanse_t h, unsigned spins, int withhold
 /* 1 if the handle's step runs the row-staged kernel, 0 for the one-cell-per-
    thread kernel, -1 for a NULL handle. */
 LBM_API int lbm_vanse_uses_row_kernel(lbm_vanse_t h);
+
+/* Launch shape of the handle's step (not in the paper; what the autotuner
+   and the benchmark record): shape[0] = kernel (0 FP64 one cell per
+   thread, 1 FP32/FP16 one cell per thread, 2 row-staged), then for the
+   row-staged kernel consumer warps, staged rows and grid blocks, for the
+   others block x, block y and grid blocks.  shape: 4 ints, caller-owned. */
+LBM_API int lbm_vanse_launch_shape(lbm_vanse_t h, int *shape);
 
 /* Time counter n and lattice description. */
 LBM_API long long lbm_vanse_steps_done(lbm_vanse_t h);

@@ -8,6 +8,7 @@
 
 namespace lbm {
 
+cudaError_t launch_step_fast_d1q3(const LatticeDev *, int, bool, int, int, const StepLaunch &, cudaStream_t);
 cudaError_t launch_step_fast_d2q9(const LatticeDev *, int, bool, int, int, const StepLaunch &, cudaStream_t);
 cudaError_t launch_step_fast_d3q19(const LatticeDev *, int, bool, int, int, const StepLaunch &, cudaStream_t);
 cudaError_t launch_step_fast_d3q27(const LatticeDev *, int, bool, int, int, const StepLaunch &, cudaStream_t);
@@ -49,6 +50,7 @@ StepLaunch make_launch(int nx, int ny, int nz, int bx, int by) {
   ls.row = 0;
   ls.row_grid = 0;
   ls.row_smem_even = ls.row_smem_odd = 0;
+  ls.row_consumers = ls.row_stages = 0;
   return ls;
 }
 
@@ -71,6 +73,7 @@ cudaError_t launch_step(const LatticeDev &h, const LatticeDev *L_dev, long long 
     case 0: return launch_step_fast_d2q9(L_dev, h.storage, odd, red, k, ls, s);
     case 1: return launch_step_fast_d3q19(L_dev, h.storage, odd, red, k, ls, s);
     case 2: return launch_step_fast_d3q27(L_dev, h.storage, odd, red, k, ls, s);
+    case 3: return launch_step_fast_d1q3(L_dev, h.storage, odd, red, k, ls, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -159,6 +162,44 @@ cudaError_t launch_shift(const LatticeDev &h, const float *eps, __half *sig, cud
   const dim3 grid((unsigned)((h.nxp + block - 1) / block), (unsigned)(work < 65535 ? work : 65535));
   shift_kernel<<<grid, block, 0, s>>>(eps, sig, h.nx, h.nxp, h.ny, h.nz, h.quad_axes, (float)h.qw0,
                                       (float)h.qw1);
+  return cudaGetLastError();
+}
+
+// Axes along which a pitched field varies: bit a of *mask is set when some
+// cell's value differs from that of its +e_a neighbour (periodic), compared
+// exactly.  One warp vote per axis, one atomicOr per warp that saw a change.
+template <class T>
+__global__ void variation_kernel(const T *f, int nx, int nxp, int ny, int nz, int dims, unsigned *mask) {
+  const long long n = (long long)nx * ny * nz;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i - threadIdx.x < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    unsigned bits = 0;
+    if (i < n) {
+      const int x = (int)(i % nx);
+      const long long r = i / nx;
+      const int y = (int)(r % ny), z = (int)(r / ny);
+      const long long row = ((long long)z * ny + y) * nxp;
+      const T v = f[row + x];
+      if (f[row + (x + 1 == nx ? 0 : x + 1)] != v) bits |= 1u;
+      if (dims > 1 && f[((long long)z * ny + (y + 1 == ny ? 0 : y + 1)) * nxp + x] != v) bits |= 2u;
+      if (dims > 2 && f[((long long)(z + 1 == nz ? 0 : z + 1) * ny + y) * nxp + x] != v) bits |= 4u;
+    }
+    const unsigned any = __reduce_or_sync(0xffffffffu, bits);
+    if ((threadIdx.x & 31) == 0 && any) atomicOr(mask, any);
+  }
+}
+
+cudaError_t launch_variation(const void *f, int is_f64, int nx, int nxp, int ny, int nz, int dims,
+                             unsigned *mask, cudaStream_t s) {
+  const long long n = (long long)nx * ny * nz;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (is_f64)
+    variation_kernel<double><<<(unsigned)blocks, 256, 0, s>>>(static_cast<const double *>(f), nx, nxp, ny, nz,
+                                                              dims, mask);
+  else
+    variation_kernel<float><<<(unsigned)blocks, 256, 0, s>>>(static_cast<const float *>(f), nx, nxp, ny, nz,
+                                                             dims, mask);
   return cudaGetLastError();
 }
 

@@ -57,7 +57,7 @@ using namespace lbm;
 
 namespace {
 
-constexpr int kTypes = 6;  // (lattice 0..2) x (storage fp32, fp16)
+constexpr int kTypes = 8;  // (lattice 0..3) x (storage fp32, fp16); D1Q3 members use the tiled kernel only
 constexpr int kBatchBlock = 256;
 constexpr int kPitchClasses = 8;                     // row pitch 64/128/256/512, with or without y/z walls
 constexpr int kRowClasses = kTypes * kPitchClasses;  // batched row kernel classes
@@ -197,6 +197,8 @@ cudaError_t launch_batch_type(int type, const BatchMember *members, const BatchT
     case 3: return launch_type<D3Q19, __half>(members, tiles, range, k, kmax, red, partials, grid, s);
     case 4: return launch_type<D3Q27, float>(members, tiles, range, k, kmax, red, partials, grid, s);
     case 5: return launch_type<D3Q27, __half>(members, tiles, range, k, kmax, red, partials, grid, s);
+    case 6: return launch_type<D1Q3, float>(members, tiles, range, k, kmax, red, partials, grid, s);
+    case 7: return launch_type<D1Q3, __half>(members, tiles, range, k, kmax, red, partials, grid, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -357,10 +359,12 @@ extern "C" int lbm_vanse_batch_add(lbm_vanse_batch_t b, lbm_vanse_t h, long long
   hm.type = type_of(m.lattice, m.storage);
   hm.row_class = -1;
   // the batched row kernel takes the member unless its lattice was created
-  // for the one-cell-per-thread kernel or its rows do not fit the kernel
+  // for the one-cell-per-thread kernel (explicitly, or by its drag law or
+  // closure), is one-dimensional, or its rows do not fit the kernel
   lbm_vanse_params p;
-  if (lbm_vanse_get_params(h, &p) == LBM_OK && p.kernel != 1 /* one cell per thread */ && m.nx >= 8 &&
-      m.nxp <= 512 && !(m.walls & 1u) && m.ncell <= 0x7fffffffLL) {
+  if (lbm_vanse_get_params(h, &p) == LBM_OK && p.kernel != 1 /* one cell per thread */ && !p.drag_model &&
+      !(p.les_cs > 0.0) && m.lattice != LBM_D1Q3 && m.nx >= 8 && m.nxp <= 512 && !(m.walls & 1u) &&
+      m.ncell <= 0x7fffffffLL) {
     const int nyf = (m.walls & 2u) ? m.ny - 2 : m.ny, nzf = (m.walls & 4u) ? m.nz - 2 : m.nz;
     const int pclass = (m.nxp <= 64 ? 0 : (m.nxp <= 128 ? 1 : (m.nxp <= 256 ? 2 : 3))) | ((m.walls & 6u) ? 4 : 0);
     const int cls = hm.type * kPitchClasses + pclass;

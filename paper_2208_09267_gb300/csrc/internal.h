@@ -61,6 +61,19 @@ struct LatticeDev {
   int withhold_copies;     // test only: the row kernel issues no copies
   int fp16_nearest;        // FP16 stores: 0 stochastic rounding, 1 nearest
   int pad3;
+  // phase-interaction drag (Ergun-type, implicit in eq. (velocity)) and the
+  // Smagorinsky closure; both zero = the plain scheme.  Doubles as given by
+  // the caller (the FP64 kernels follow the reference's operation order),
+  // floats premultiplied for the FP32 kernels.
+  int drag_model;          // 0 none, 1 Ergun-type
+  int les;                 // Smagorinsky closure on
+  double drag_c1, drag_c2, drag_d;  // viscous / inertial coefficients, particle diameter
+  double tau0;             // the laminar relaxation time tau
+  double les_cs;           // Smagorinsky constant C
+  float drag_linf;         // c1 nu / d^2
+  float drag_qf;           // c2 / d
+  float les_cf;            // 18 sqrt(2) C^2
+  float tau0f;
 };
 
 constexpr int kRedWidth = 12;  // M0, mom x/y/z, |du|^2, |u|^2, nan, F x/y/z, spare x2
@@ -72,6 +85,9 @@ struct StepLaunch {
   int row;
   int row_grid;
   int row_smem_even, row_smem_odd;
+  // row kernel shape: consumer warps and input stages per block (0 = the
+  // compiled default; the planner writes back what it chose)
+  int row_consumers, row_stages;
 };
 
 // Plan the row-staged kernel for a lattice: fills ls.row* and returns 1 when
@@ -119,6 +135,11 @@ cudaError_t launch_shift(const LatticeDev &host_mirror, const float *eps, __half
 // *first_bad must hold a value >= n beforehand.
 cudaError_t launch_validate(const void *data, long long n, int is_f64, int unit, long long *first_bad,
                             cudaStream_t s);
+
+// OR into *mask the axes (bit a = axis a < dims) along which the pitched
+// field f (float or double, nx*ny*nz values at row pitch nxp) varies.
+cudaError_t launch_variation(const void *f, int is_f64, int nx, int nxp, int ny, int nz, int dims,
+                             unsigned *mask, cudaStream_t s);
 
 // Float -> double / double -> float conversions for field uploads.
 cudaError_t launch_convert_f2d(const float *in, double *out, long long n, cudaStream_t s);

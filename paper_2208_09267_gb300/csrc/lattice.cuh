@@ -1,5 +1,7 @@
 // lattice.cuh -- discrete velocity sets for the device kernels.
 //
+// D1Q3: the one-dimensional stencil (Sec. 2.2 names one-dimensional
+// stencils beside the 2D and 3D ones); textbook weights 2/3, 1/6.
 // D2Q9: Sec. 2.2 Table "latt_par" (weights 4/9, 1/9, 1/36).
 // D3Q27: Sec. 2.2 Table "latt_3d" (8/27, 2/27, 1/54, 1/216).
 // D3Q19: not in the paper; textbook weights 1/3, 1/18, 1/36.
@@ -32,7 +34,17 @@ __host__ __device__ constexpr int d2_c(int i, int a) {
   return a < 2 ? t[i][a] : 0;
 }
 
+__host__ __device__ constexpr int d1_c(int i, int a) { return a == 0 ? (i == 1 ? 1 : (i == 2 ? -1 : 0)) : 0; }
+
 __host__ __device__ constexpr int opp_of(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+
+struct D1Q3 {
+  static constexpr int Q = 3;
+  static constexpr int D = 1;
+  static constexpr int id = 3;
+  __host__ __device__ static constexpr int c(int i, int a) { return d1_c(i, a); }
+  __host__ __device__ static constexpr double w(int i) { return i == 0 ? 2.0 / 3.0 : 1.0 / 6.0; }
+};
 
 struct D2Q9 {
   static constexpr int Q = 9;

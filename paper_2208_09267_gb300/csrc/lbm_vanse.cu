@@ -22,8 +22,8 @@ namespace {
 
 thread_local std::string g_last_error;
 
-const int kQ[3] = {9, 19, 27};
-const int kD[3] = {2, 3, 3};
+const int kQ[4] = {9, 19, 27, 3};
+const int kD[4] = {2, 3, 3, 1};
 const size_t kElem[3] = {8, 4, 2};
 constexpr int kGraphChunk = 64;  // steps per captured graph (even)
 constexpr size_t kRowGridBound = 4096;  // upper bound of the row kernel's grid
@@ -108,14 +108,18 @@ extern "C" int lbm_vanse_params_default(lbm_vanse_params *p) {
 static int validate_params(const lbm_vanse_params *p, std::string &why) {
   char buf[256];
   if (!p) { why = "params is NULL"; return 0; }
-  if (p->lattice < 0 || p->lattice > 2) { why = "lattice must be LBM_D2Q9, LBM_D3Q19 or LBM_D3Q27"; return 0; }
+  if (p->lattice < 0 || p->lattice > 3) {
+    why = "lattice must be LBM_D2Q9, LBM_D3Q19, LBM_D3Q27 or LBM_D1Q3";
+    return 0;
+  }
   if (p->storage < 0 || p->storage > 2) { why = "storage must be LBM_FP64, LBM_FP32 or LBM_FP16_SHIFTED"; return 0; }
   if (p->nx < 1 || p->ny < 1 || p->nz < 1) { why = "nx, ny, nz must be >= 1"; return 0; }
   if (p->lattice == LBM_D2Q9 && p->nz != 1) { why = "D2Q9 needs nz = 1"; return 0; }
+  if (p->lattice == LBM_D1Q3 && (p->ny != 1 || p->nz != 1)) { why = "D1Q3 needs ny = nz = 1"; return 0; }
   if (p->ny > 65535 * 256 || p->nz > 65535) { why = "ny or nz too large for the launch grid"; return 0; }
   if (!(p->tau > 0.5) || !std::isfinite(p->tau)) { why = "tau must be a finite value > 0.5"; return 0; }
   if (!(p->rho0 > 0.0) || !std::isfinite(p->rho0)) { why = "rho0 must be positive"; return 0; }
-  const unsigned axes_mask = p->lattice == LBM_D2Q9 ? 3u : 7u;
+  const unsigned axes_mask = (1u << kD[p->lattice]) - 1u;
   if (p->quad_axes & ~axes_mask) { why = "quad_axes names an axis the lattice does not have"; return 0; }
   if (p->walls & ~axes_mask) { why = "walls names an axis the lattice does not have"; return 0; }
   const unsigned qa = p->quad_axes ? p->quad_axes : axes_mask;
@@ -138,6 +142,23 @@ static int validate_params(const lbm_vanse_params *p, std::string &why) {
   }
   if (p->kernel < 0 || p->kernel > 2) { why = "kernel must be 0, 1 or 2"; return 0; }
   if (p->fp16_rounding < 0 || p->fp16_rounding > 1) { why = "fp16_rounding must be 0 or 1"; return 0; }
+  if (p->quad_auto < 0 || p->quad_auto > 1) { why = "quad_auto must be 0 or 1"; return 0; }
+  if (p->drag_model < 0 || p->drag_model > 1) { why = "drag_model must be 0 or 1"; return 0; }
+  if (p->drag_model &&
+      !(std::isfinite(p->drag_c1) && std::isfinite(p->drag_c2) && p->drag_c1 >= 0.0 && p->drag_c2 >= 0.0 &&
+        std::isfinite(p->drag_d) && p->drag_d > 0.0)) {
+    why = "drag needs finite c1, c2 >= 0 and a particle diameter d > 0";
+    return 0;
+  }
+  if (!(std::isfinite(p->les_cs) && p->les_cs >= 0.0)) { why = "les_cs must be a finite value >= 0"; return 0; }
+  if (p->row_consumers < 0 || p->row_consumers > 32 || p->row_stages < 0 || p->row_stages > 16) {
+    why = "row_consumers must be in 0..32 and row_stages in 0..16";
+    return 0;
+  }
+  if (p->kernel == 2 && (p->drag_model || p->les_cs > 0.0)) {
+    why = "drag and the Smagorinsky closure run in the one-cell-per-thread kernel (kernel 0 or 1)";
+    return 0;
+  }
   if (p->kernel == 2 && p->storage == LBM_FP64) { why = "the row-staged kernel needs FP32 or FP16 storage"; return 0; }
   if (p->block_x < 0 || p->block_y < 0 || p->block_x * p->block_y > 256 ||
       (p->block_x > 0 && p->block_x % 32 != 0 && p->block_x * p->block_y % 32 != 0)) {
@@ -252,7 +273,7 @@ extern "C" int lbm_vanse_create(const lbm_vanse_params *p, lbm_vanse_t *out) {
   h->nxp = pitch_of(p->nx);
   h->Ni = (long long)h->nxp * p->ny * p->nz;
   h->field_elem = p->storage == LBM_FP64 ? 8 : 4;
-  const unsigned axes_mask = p->lattice == LBM_D2Q9 ? 3u : 7u;
+  const unsigned axes_mask = (1u << kD[p->lattice]) - 1u;
   const unsigned qa = p->quad_axes ? p->quad_axes : axes_mask;
   const int qd = p->quad_dim ? p->quad_dim : __builtin_popcount(qa);
   h->p.quad_axes = qa;
@@ -277,6 +298,20 @@ extern "C" int lbm_vanse_create(const lbm_vanse_params *p, lbm_vanse_t *out) {
   m.fp16_nearest = p->fp16_rounding == 1 ? 1 : 0;
   m.qw0 = lbm::quad_w0(qd);
   m.qw1 = lbm::quad_w1(qd);
+  m.tau0 = p->tau;
+  m.tau0f = (float)p->tau;
+  m.drag_model = p->drag_model;
+  if (p->drag_model) {
+    m.drag_c1 = p->drag_c1;
+    m.drag_c2 = p->drag_c2;
+    m.drag_d = p->drag_d;
+    const double nu = (p->tau - 0.5) / 3.0;
+    m.drag_linf = (float)(p->drag_c1 * nu / (p->drag_d * p->drag_d));
+    m.drag_qf = (float)(p->drag_c2 / p->drag_d);
+  }
+  m.les = p->les_cs > 0.0 ? 1 : 0;
+  m.les_cs = p->les_cs;
+  m.les_cf = (float)(18.0 * std::sqrt(2.0) * p->les_cs * p->les_cs);
   if (p->storage == LBM_FP16_SHIFTED) {
     m.scale = ldexpf(1.0f, p->fp16_scale_log2);
     m.inv_scale = ldexpf(1.0f, -p->fp16_scale_log2);
@@ -286,7 +321,9 @@ extern "C" int lbm_vanse_create(const lbm_vanse_params *p, lbm_vanse_t *out) {
 
   h->ls = lbm::make_launch(p->nx, p->ny, p->nz, p->block_x, p->block_y);
   h->nblocks = (int)(h->ls.grid.x * h->ls.grid.y * h->ls.grid.z);
-  if (p->kernel != 1 && p->storage != LBM_FP64) {
+  h->ls.row_consumers = p->row_consumers;
+  h->ls.row_stages = p->row_stages;
+  if (p->kernel != 1 && p->storage != LBM_FP64 && !p->drag_model && !(p->les_cs > 0.0)) {
     const int ok = lbm::plan_row_kernel(p->lattice, p->storage, p->nx, h->nxp, p->ny, p->nz, p->walls, h->ls);
     if (!ok && p->kernel == 2) {
       delete h;
@@ -467,7 +504,36 @@ static int ensure_deps_buf(lbm_vanse_t h, int b) {
 // Make the spare phi_ref / d_t phi buffers (already filled and checked) the
 // current ones: the shift sigma of the new phi_ref is computed into the
 // spare shift buffer, and the next step decodes with the old one.
+// quad_auto: the quadrature rule from the directions in which phi_ref (and
+// d_t phi) vary (Sec. 2.2, eq. (quad) and Table "weights"), every lattice
+// axis when phi is uniform.  Scans buffer `b` on the device; synchronises.
+static int choose_quadrature(lbm_vanse_t h, int b, int has_deps) {
+  unsigned *mask = reinterpret_cast<unsigned *>(h->stats_dev + 40);
+  CUDA_TRY(h, cudaMemsetAsync(mask, 0, sizeof(unsigned), h->stream));
+  const int f64 = h->field_elem == 8;
+  CUDA_TRY(h, lbm::launch_variation(h->eps_buf[b], f64, h->p.nx, h->nxp, h->p.ny, h->p.nz, h->D, mask, h->stream));
+  if (has_deps)
+    CUDA_TRY(h, lbm::launch_variation(h->deps_buf[b], f64, h->p.nx, h->nxp, h->p.ny, h->p.nz, h->D, mask,
+                                      h->stream));
+  unsigned *host = reinterpret_cast<unsigned *>(h->stats_host + 40);
+  CUDA_TRY(h, cudaMemcpyAsync(host, mask, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  const unsigned all = (1u << h->D) - 1u;
+  const unsigned qa = (*host & all) ? (*host & all) : all;
+  const int qd = __builtin_popcount(qa);
+  h->p.quad_axes = qa;
+  h->p.quad_dim = qd;
+  h->h.quad_axes = qa;
+  h->h.qw0 = lbm::quad_w0(qd);
+  h->h.qw1 = lbm::quad_w1(qd);
+  return LBM_OK;
+}
+
 static int adopt_epsilon(lbm_vanse_t h, int next, int has_deps, long long n_ref) {
+  if (h->p.quad_auto) {
+    const int rc = choose_quadrature(h, next, has_deps);
+    if (rc) return rc;
+  }
   h->h.has_deps = has_deps;
   h->eps_cur = next;
   h->h.n_eps = n_ref;
@@ -1112,6 +1178,15 @@ extern "C" int lbm_vanse_set_wait_limit(lbm_vanse_t h, unsigned spins, int withh
 }
 
 extern "C" int lbm_vanse_uses_row_kernel(lbm_vanse_t h) { return h ? (h->ls.row ? 1 : 0) : -1; }
+
+extern "C" int lbm_vanse_launch_shape(lbm_vanse_t h, int *shape) {
+  if (!h || !shape) return fail(h, LBM_EINVAL, "NULL argument");
+  shape[0] = h->ls.row ? 2 : (h->p.storage == LBM_FP64 ? 0 : 1);
+  shape[1] = h->ls.row ? h->ls.row_consumers : (int)h->ls.block.x;
+  shape[2] = h->ls.row ? h->ls.row_stages : (int)h->ls.block.y;
+  shape[3] = h->ls.row ? h->ls.row_grid : (int)(h->ls.grid.x * h->ls.grid.y * h->ls.grid.z);
+  return LBM_OK;
+}
 
 // ---------------------------------------------------------------- read-back without allocation
 

@@ -152,8 +152,35 @@ __device__ __forceinline__ void macro_exact(const LatticeDev &L, long long n, co
     if (L.has_force) fext = fext + force_at<LAT>(L, a, k, dnf);
     m.F[a] = (a < D) ? fext + pc * grad : 0.0;
   }
+  if (!L.drag_model) {
 #pragma unroll
-  for (int a = 0; a < 3; ++a) m.u[a] = (m.J[a] + 0.5 * m.F[a]) / m.M0;
+    for (int a = 0; a < 3; ++a) m.u[a] = (m.J[a] + 0.5 * m.F[a]) / m.M0;
+    return;
+  }
+  // phase-interaction drag F_D = -(b_lin + b_q |u|) u (Ergun-type law of a
+  // fixed bed, Sec. 2.2's force sum), implicit in eq. (velocity): with
+  // b = J + F/2 the speed s = |u| is the positive root of
+  // (b_q/2) s^2 + (M0 + b_lin/2) s - |b| = 0, u = b / (M0 + b_lin/2 + b_q s/2)
+  const double one_m = 1.0 - e_c;
+  const double nu = (L.tau0 - 0.5) / 3.0;
+  const double blin = m.rho * L.drag_c1 * one_m * one_m * nu / (e_c * L.drag_d * L.drag_d);
+  const double bq = m.rho * L.drag_c2 * one_m / L.drag_d;
+  double b[3], bn = 0.0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    b[a] = m.J[a] + 0.5 * m.F[a];
+    bn = bn + b[a] * b[a];
+  }
+  bn = sqrt(bn);
+  const double A = m.M0 + 0.5 * blin;
+  const double sp = 2.0 * bn / (A + sqrt(A * A + 2.0 * bq * bn));
+  const double den = A + 0.5 * bq * sp;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    m.u[a] = b[a] / den;
+    const double fd = (blin + bq * sp) * m.u[a];
+    m.F[a] = (a < D) ? m.F[a] - fd : 0.0;
+  }
 }
 
 template <class LAT>
@@ -226,7 +253,33 @@ __global__ void __launch_bounds__(256) step_exact_kernel(const LatticeDev *__res
       acc.v[8] += m.F[1];
       acc.v[9] += m.F[2];
     }
-    const double omega = L.omega, cf = L.cf;
+    double omega = L.omega, cf = L.cf;
+    if (L.les) {
+      // Smagorinsky closure: Pi^neq_ab = sum_i xi_ia xi_ib (f_i - f_i^eq),
+      // tau_eff = (tau + sqrt(tau^2 + 18 sqrt(2) C^2 |Pi^neq| / M0)) / 2
+      double pi[3][3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) pi[a][b] = 0.0;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const double fneq = f[i] - feq_exact<LAT>(i, m.M0, m.u, usq);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) pi[a][b] = pi[a][b] + (double)LAT::c(i, a) * (double)LAT::c(i, b) * fneq;
+      }
+      double q2 = 0.0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) q2 = q2 + pi[a][b] * pi[a][b];
+      const double teff =
+          0.5 * (L.tau0 + sqrt(L.tau0 * L.tau0 + 18.0 * sqrt(2.0) * L.les_cs * L.les_cs * sqrt(q2) / m.M0));
+      omega = 1.0 / teff;
+      cf = 1.0 - 0.5 / teff;
+    }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const double feq = feq_exact<LAT>(i, m.M0, m.u, usq);
@@ -389,6 +442,7 @@ cudaError_t launch_step_exact(int lattice, const LatticeDev *L_dev, bool odd, in
     case 0: return launch_exact_lat<D2Q9>(L_dev, odd, red, k, ls, s);
     case 1: return launch_exact_lat<D3Q19>(L_dev, odd, red, k, ls, s);
     case 2: return launch_exact_lat<D3Q27>(L_dev, odd, red, k, ls, s);
+    case 3: return launch_exact_lat<D1Q3>(L_dev, odd, red, k, ls, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -403,6 +457,7 @@ cudaError_t launch_moments(const LatticeDev &h, const LatticeDev *L_dev, long lo
     case 0: moments_kernel<D2Q9><<<ls.grid, ls.block, 0, s>>>(L_dev, rho, p, u, rho_f, p_f, u_f); break;
     case 1: moments_kernel<D3Q19><<<ls.grid, ls.block, 0, s>>>(L_dev, rho, p, u, rho_f, p_f, u_f); break;
     case 2: moments_kernel<D3Q27><<<ls.grid, ls.block, 0, s>>>(L_dev, rho, p, u, rho_f, p_f, u_f); break;
+    case 3: moments_kernel<D1Q3><<<ls.grid, ls.block, 0, s>>>(L_dev, rho, p, u, rho_f, p_f, u_f); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -415,6 +470,7 @@ cudaError_t launch_init(const LatticeDev &h, const LatticeDev *L_dev, long long,
     case 0: init_kernel<D2Q9><<<ls.grid, ls.block, 0, s>>>(L_dev, p0, u0, mode); break;
     case 1: init_kernel<D3Q19><<<ls.grid, ls.block, 0, s>>>(L_dev, p0, u0, mode); break;
     case 2: init_kernel<D3Q27><<<ls.grid, ls.block, 0, s>>>(L_dev, p0, u0, mode); break;
+    case 3: init_kernel<D1Q3><<<ls.grid, ls.block, 0, s>>>(L_dev, p0, u0, mode); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -427,6 +483,7 @@ cudaError_t launch_get_populations(const LatticeDev &h, const LatticeDev *L_dev,
     case 0: getpop_kernel<D2Q9><<<ls.grid, ls.block, 0, s>>>(L_dev, f); break;
     case 1: getpop_kernel<D3Q19><<<ls.grid, ls.block, 0, s>>>(L_dev, f); break;
     case 2: getpop_kernel<D3Q27><<<ls.grid, ls.block, 0, s>>>(L_dev, f); break;
+    case 3: getpop_kernel<D1Q3><<<ls.grid, ls.block, 0, s>>>(L_dev, f); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -18,7 +18,9 @@
 //        f^eq_i/w_i - s_x = dM + M0 (3 cu + 4.5 cu^2 - 1.5 u.u),
 //        Omega_i/w_i = (1 - 1/(2 tau)) (3 (xi.F - u.F) + 9 (xi.u)(xi.F)),
 //        d*_i = d_i + (d^eq_i - d_i)/tau + Omega_i/w_i;
-//   8. encode against the shift of the slot's storage cell and store.
+//   8. encode against the shift of the slot's storage cell and store; FP32
+//      stores the rest population last, with the value that keeps the mass
+//      of the stored values (the zeroth moment) exactly balanced.
 //
 // AA pattern (in place, one array): at even n a cell reads its own slots i
 // and writes f*_i to its own slot opp(i); at odd n it reads slot opp(i) of
@@ -191,21 +193,27 @@ __device__ __forceinline__ void update_cell_fast(const LatticeDev &L, long long 
   const float inv_scale = L.inv_scale, scale = L.scale;
   const float s_x = rho0 * __half2float(srd[cell]);
 
-  // 1. load and decode
-  float d[Q];
+  // 1. load and decode.  FP32 keeps the stored values q_i as read for the
+  //    mass balance of step 8, and after a phi refresh the difference of the
+  //    read and write shifts of the slots it reads.
+  constexpr bool kMassFix = sizeof(ST) == 4;
+  const bool reshift = srd != swr;
+  float d[Q], qraw[Q];
+  float frame = 0.f;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    constexpr int dummy = 0;
-    (void)dummy;
     const int cx = LAT::c(i, 0), cy = LAT::c(i, 1), cz = LAT::c(i, 2);
-    if (!ODD || i == 0) {
-      d[i] = PopIO<ST>::ld(pop + (long long)i * plane + cell) * inv_scale;
-    } else if (walls && solid_at(walls, x, y, z, -cx, -cy, -cz, nx, ny, nz)) {
-      d[i] = PopIO<ST>::ld(pop + (long long)i * plane + cell) * inv_scale;
+    if (!ODD || i == 0 || (walls && solid_at(walls, x, y, z, -cx, -cy, -cz, nx, ny, nz))) {
+      qraw[i] = PopIO<ST>::ld(pop + (long long)i * plane + cell);
+      d[i] = qraw[i] * inv_scale;
+      if (kMassFix && reshift) frame = fmaf((float)LAT::w(i), fmaf(-rho0, __half2float(swr[cell]), s_x), frame);
     } else {
       const long long m = C.at(-cx, -cy, -cz);
-      d[i] = fmaf(PopIO<ST>::ld(pop + (long long)opp_of(i) * plane + m), inv_scale,
-                  fmaf(rho0, __half2float(srd[m]), -s_x));
+      qraw[i] = PopIO<ST>::ld(pop + (long long)opp_of(i) * plane + m);
+      const float sm = __half2float(srd[m]);
+      d[i] = fmaf(qraw[i], inv_scale, fmaf(rho0, sm, -s_x));
+      if (kMassFix && reshift)
+        frame = fmaf((float)LAT::w(i), rho0 * (sm - __half2float(swr[m])), frame);
     }
   }
 
@@ -274,7 +282,27 @@ __device__ __forceinline__ void update_cell_fast(const LatticeDev &L, long long 
   }
 
   // 6. eq. (velocity)
-  const float invM = 1.0f / M0;
+  float invM = 1.0f / M0;
+  if (L.drag_model) {
+    // phase-interaction drag F_D = -(b_lin + b_q |u|) u (Ergun-type law of a
+    // fixed bed), implicit in eq. (velocity): with b = J + F/2 the speed s =
+    // |u| is the positive root of (b_q/2) s^2 + (M0 + b_lin/2) s - |b| = 0
+    // and u = b / (M0 + b_lin/2 + b_q s/2); F_D joins the force sum
+    const float one_m = 1.0f - e_c;
+    const float blin = rho * L.drag_linf * one_m * one_m / e_c;
+    const float bq = rho * L.drag_qf * one_m;
+    const float b0 = fmaf(0.5f, F0, j0), b1 = fmaf(0.5f, F1, j1), b2 = D == 3 ? fmaf(0.5f, F2, j2) : 0.f;
+    const float bn = sqrtf(fmaf(b0, b0, fmaf(b1, b1, b2 * b2)));
+    const float A = fmaf(0.5f, blin, M0);
+    const float sp = 2.0f * bn / (A + sqrtf(fmaf(A, A, 2.0f * bq * bn)));
+    invM = 1.0f / fmaf(0.5f * bq, sp, A);
+    const float beta = fmaf(bq, sp, blin);
+    F0 = fmaf(-beta * b0, invM, F0);
+    F1 = fmaf(-beta * b1, invM, F1);
+    if (D == 3) F2 = fmaf(-beta * b2, invM, F2);
+    // then (J + F/2) / M0 = b / (A + b_q s/2): the velocity below
+    invM = 1.0f / M0;
+  }
   const float u0 = (j0 + 0.5f * F0) * invM;
   const float u1 = (j1 + 0.5f * F1) * invM;
   const float u2 = D == 3 ? (j2 + 0.5f * F2) * invM : 0.f;
@@ -307,13 +335,49 @@ __device__ __forceinline__ void update_cell_fast(const LatticeDev &L, long long 
     acc.v[9] += (double)F2;
   }
 
-  // 7. collide (deviation form) and 8. stream
-  const float omega = L.omegaf, cf = L.cff;
-  const bool reshift = srd != swr;
+  // 7. collide (deviation form) and 8. stream.  d*_i = d_i + (omega (d^eq_i
+  //    - d_i) + Omega_i/w_i): one rounding at the size of d_i.  FP32 then
+  //    balances the mass of the stored values through the rest population,
+  //    stored last: every slot the cell reads is a slot it writes (AA
+  //    pattern), so w_0 V_0 = w_0 q_0 + sum_{i>0} w_i (q_i - V_i) + frame
+  //    conserves the zeroth moment of the stored state up to one rounding.
+  float omega = L.omegaf, cf = L.cff;
+  if (L.les) {
+    // Smagorinsky closure: tau_eff = (tau + sqrt(tau^2 + 18 sqrt(2) C^2
+    // |Pi^neq| / M0)) / 2 with Pi^neq_ab = sum_i xi_ia xi_ib (f_i - f_i^eq);
+    // in deviation form f_i - f_i^eq = w_i (d_i - d^eq_i)
+    float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const int cx = LAT::c(i, 0), cy = LAT::c(i, 1), cz = LAT::c(i, 2);
+      float cu = 0.f;
+      if (cx == 1) cu += u0;
+      if (cx == -1) cu -= u0;
+      if (cy == 1) cu += u1;
+      if (cy == -1) cu -= u1;
+      if (cz == 1) cu += u2;
+      if (cz == -1) cu -= u2;
+      const float deq = fmaf(M0, fmaf(cu, fmaf(4.5f, cu, 3.0f), -1.5f * usq), dM);
+      const float fn = (float)LAT::w(i) * (d[i] - deq);
+      if (cx) pxx += fn;
+      if (cy) pyy += fn;
+      if (cz) pzz += fn;
+      if (cx && cy) pxy = fmaf((float)(cx * cy), fn, pxy);
+      if (cx && cz) pxz = fmaf((float)(cx * cz), fn, pxz);
+      if (cy && cz) pyz = fmaf((float)(cy * cz), fn, pyz);
+    }
+    const float q = sqrtf(fmaf(pxx, pxx, fmaf(pyy, pyy, fmaf(pzz, pzz, 2.0f * fmaf(pxy, pxy, fmaf(pxz, pxz, pyz * pyz))))));
+    const float t0 = L.tau0f;
+    const float teff = 0.5f * (t0 + sqrtf(fmaf(t0, t0, L.les_cf * q / M0)));
+    omega = 1.0f / teff;
+    cf = 1.0f - 0.5f / teff;
+  }
   SRng rng((unsigned)cell, n);
   const bool sr = L.fp16_nearest == 0;
+  float R = frame;
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
+  for (int ii = 1; ii <= Q; ++ii) {
+    const int i = ii == Q ? 0 : ii;
     const int cx = LAT::c(i, 0), cy = LAT::c(i, 1), cz = LAT::c(i, 2);
     float cu = 0.f, cF = 0.f;
     if (cx == 1) { cu += u0; cF += F0; }
@@ -322,29 +386,30 @@ __device__ __forceinline__ void update_cell_fast(const LatticeDev &L, long long 
     if (cy == -1) { cu -= u1; cF -= F1; }
     if (cz == 1) { cu += u2; cF += F2; }
     if (cz == -1) { cu -= u2; cF -= F2; }
-    const float pm1 = cu * fmaf(4.5f, cu, 3.0f) - 1.5f * usq;
+    const float pm1 = fmaf(cu, fmaf(4.5f, cu, 3.0f), -1.5f * usq);
     const float deq = fmaf(M0, pm1, dM);
     const float src = cf * fmaf(9.0f * cu, cF, 3.0f * (cF - uF));
-    const float ds = fmaf(omega, deq - d[i], d[i]) + src;
+    const float ds = d[i] + fmaf(omega, deq - d[i], src);
     // the shift difference uses the exact product rho0*sigma (FMA) exactly
     // as the decode does, so that a stored value round-trips
-    if (!ODD) {
-      float q = ds;
+    ST *slot;
+    float q;
+    if (!ODD || i == 0 || (walls && solid_at(walls, x, y, z, cx, cy, cz, nx, ny, nz))) {
+      q = ds;
       if (reshift) q += fmaf(-rho0, __half2float(swr[cell]), s_x);
-      store_pop<ST>(pop + (long long)opp_of(i) * plane + cell, q * scale, rng, sr);
-    } else if (i == 0) {
-      float q = ds;
-      if (reshift) q += fmaf(-rho0, __half2float(swr[cell]), s_x);
-      store_pop<ST>(pop + cell, q * scale, rng, sr);
-    } else if (walls && solid_at(walls, x, y, z, cx, cy, cz, nx, ny, nz)) {
-      float q = ds;
-      if (reshift) q += fmaf(-rho0, __half2float(swr[cell]), s_x);
-      store_pop<ST>(pop + (long long)opp_of(i) * plane + cell, q * scale, rng, sr);
+      slot = pop + (long long)opp_of(i) * plane + cell;
     } else {
       const long long m = C.at(cx, cy, cz);
-      const float q = ds + fmaf(-rho0, __half2float(swr[m]), s_x);
-      store_pop<ST>(pop + (long long)i * plane + m, q * scale, rng, sr);
+      q = ds + fmaf(-rho0, __half2float(swr[m]), s_x);
+      slot = pop + (long long)i * plane + m;
     }
+    float v = q;
+    if (kMassFix) {
+      // FP32 (scale 1): the stored value is q itself
+      if (i != 0) R = fmaf((float)LAT::w(i), qraw[i] - q, R);
+      else v = fmaf(R, (float)(1.0 / LAT::w(0)), qraw[0]);
+    }
+    store_pop<ST>(slot, v * scale, rng, sr);
   }
 }
 

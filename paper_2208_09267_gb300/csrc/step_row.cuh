@@ -249,10 +249,14 @@ __device__ __forceinline__ void issue_copy(const RowCopy &c, unsigned char *stag
 // RS: the step after a phi refresh decodes with the old shift and encodes
 // with the new one ("reshift").  0: no refresh pending, 1: pending (both
 // known at launch), 2: read it from the descriptor.
-template <class LAT, class ST, bool ODD, bool RED, bool WALLS, int PITCH, int RS = 2>
+// OUTS: the updated populations go to the output stage `ostage` in shared
+// memory (row i holds f*_i at the position of its storage cell in the
+// destination row) instead of straight to global memory; a storer warp
+// writes the rows back with bulk copies.
+template <class LAT, class ST, bool ODD, bool RED, bool WALLS, int PITCH, int RS = 2, bool OUTS = false>
 __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsigned char *stage,
                                                  const RowCtx &rc, long long n, float dn, float dn_force,
-                                                 int x, RedAcc &acc) {
+                                                 int x, RedAcc &acc, unsigned char *ostage = nullptr) {
   using Lay = RowLayout<LAT, ST, ODD, PITCH>;
   constexpr int Q = LAT::Q, D = LAT::D;
   // FP16 stores deviations times 2^k.  The update below runs in those
@@ -261,6 +265,9 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
   // those of the unscaled arithmetic, without a multiply per population on
   // load and store.
   constexpr bool kScaled = sizeof(ST) < 4;
+  // FP32: per-population collision in the change form and a local mass
+  // balance through the rest population (step 8 below)
+  constexpr bool kMassFix = sizeof(ST) == 4;
   const int nx = L.nx;
   const ST *prow = reinterpret_cast<const ST *>(stage);
   const __half *srow = reinterpret_cast<const __half *>(stage + Lay::kSigOff);
@@ -302,21 +309,28 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
   //    - s_x (exact product in the FMA; the encode below uses the same form,
   //    so the round trip is exact up to the final rounding).  Own-cell values
   //    need no shift.
-  float d[Q], delta[Q];
+  //    FP32 also keeps the stored values q_i as read (the mass balance of
+  //    step 8 is taken on them) and, after a phi refresh, the difference
+  //    between the read and write shifts of the slots it reads.
+  float d[Q], delta[Q], qraw[Q];
+  float frame = 0.f;  // sum_i w_i rho0 (sigma_rd - sigma_wr) of the slots read (FP32, refresh steps)
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int cx = LAT::c(i, 0), cy = LAT::c(i, 1), cz = LAT::c(i, 2);
     const bool own = OWN_SRC(i);
     const float q = PopIO<ST>::ld(prow + i * PITCH + (own ? x : xs[1 - cx]));
+    qraw[i] = q;
     if (own) {
       delta[i] = 0.f;
       d[i] = q;
+      if (kMassFix && reshift) frame = fmaf((float)LAT::w(i), fmaf(-rho0, sig_own, s_x), frame);
     } else {
-      const float sm =
-          reshift ? __half2float(srd[rc.base[1 - cz][1 - cy] + xs[1 - cx]]) : SIG_AT(-cy, -cz, xs[1 - cx]);
+      const float sw = SIG_AT(-cy, -cz, xs[1 - cx]);
+      const float sm = reshift ? __half2float(srd[rc.base[1 - cz][1 - cy] + xs[1 - cx]]) : sw;
       delta[i] = fmaf(rho0, sm, -s_x);
       // delta 2^k is exact, so the FMA rounds once, as q + delta 2^k does
       d[i] = kScaled ? fmaf(delta[i], scale, q) : q + delta[i];
+      if (kMassFix && reshift) frame = fmaf((float)LAT::w(i), rho0 * (sm - sw), frame);
     }
   }
 
@@ -432,7 +446,8 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
   SRng rng((unsigned)cell, n);
   const bool sr = L.fp16_nearest == 0;
   // encode population i (compile-time index) with post-collision deviation
-  // DSTAR (storage units): P_ = its slot, V_ = the value to store
+  // DSTAR (storage units): P_ = its slot, V_ = the value to store against
+  // the shift of the cell whose memory holds it
 #define ENCODE_POP(i, DSTAR, P_, V_)                                                               \
   ST *P_;                                                                                          \
   float V_;                                                                                        \
@@ -441,7 +456,7 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
     const float ds_ = (DSTAR);                                                                     \
     if (OWN_DST(i)) {                                                                              \
       V_ = reshift ? fmaf(enc_own, sc, ds_) : ds_;                                                 \
-      P_ = (pop + opp_of(i) * plane) + cell;                                                       \
+      P_ = OUTS ? reinterpret_cast<ST *>(ostage) + (i) * PITCH + x : (pop + opp_of(i) * plane) + cell; \
     } else {                                                                                       \
       const int xm_ = xs[1 + cx_];                                                                 \
       float enc_;                                                                                  \
@@ -450,9 +465,53 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
       else                                                                                         \
         enc_ = fmaf(-rho0, SIG_AT(cy_, cz_, xm_), s_x);                                            \
       V_ = fmaf(enc_, sc, ds_);                                                                    \
-      P_ = (pop + (i) * plane) + (rc.base[1 + cz_][1 + cy_] + xm_);                                \
+      P_ = OUTS ? reinterpret_cast<ST *>(ostage) + (i) * PITCH + xm_                               \
+                : (pop + (i) * plane) + (rc.base[1 + cz_][1 + cy_] + xm_);                         \
     }                                                                                              \
   }
+  if (kMassFix) {
+    // FP32.  d*_i = d_i + (omega (d^eq_i - d_i) + Omega_i/w_i): the final sum
+    // is the only rounding at the size of d_i (the bracket is the small
+    // non-equilibrium change).  Then the mass the stored values carry is
+    // balanced exactly: every slot the cell reads is a slot it writes (AA
+    // pattern; the same set of storage cells, so the shift terms cancel
+    // except after a refresh), hence
+    //   w_0 V_0 = w_0 q_0 + sum_{i>0} w_i (q_i - V_i) + frame
+    // with the stored values V_i as rounded.  The rest population absorbs
+    // the rounding of the others: the zeroth moment of the stored state is
+    // conserved cell by cell up to one rounding, instead of drifting with
+    // the rounding of every population.
+    float R = frame;
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+      const int cx = LAT::c(i, 0), cy = LAT::c(i, 1), cz = LAT::c(i, 2);
+      float cu = 0.f, cF = 0.f;
+      if (cx == 1) { cu += u0; cF += F0; }
+      if (cx == -1) { cu -= u0; cF -= F0; }
+      if (cy == 1) { cu += u1; cF += F1; }
+      if (cy == -1) { cu -= u1; cF -= F1; }
+      if (cz == 1) { cu += u2; cF += F2; }
+      if (cz == -1) { cu -= u2; cF -= F2; }
+      // d^eq of the pair: dM + M0 (+-3 cu + 4.5 cu^2 - 1.5 u.u)
+      const float deqa = fmaf(M0, fmaf(cu, fmaf(4.5f, cu, 3.0f), m15usq), dM);
+      const float deqb = fmaf(M0, fmaf(cu, fmaf(4.5f, cu, -3.0f), m15usq), dM);
+      // Guo term / w of the pair: cf (9 cu cF - 3 u.F) +- 3 cf cF
+      // (every sum written as an explicit FMA: the rounding is then the same
+      // in every instantiation of this code, single-lattice and batched)
+      const float sA = fmaf(cf9 * cu, cF, m3uF_s);
+      const float sa = fmaf(cf3, cF, sA), sb = fmaf(-cf3, cF, sA);
+      ENCODE_POP(i, d[i] + fmaf(omega, deqa - d[i], sa), pa_, va_);
+      ENCODE_POP(i + 1, d[i + 1] + fmaf(omega, deqb - d[i + 1], sb), pb_, vb_);
+      PopIO<ST>::st(pa_, va_);
+      PopIO<ST>::st(pb_, vb_);
+      const float w = (float)LAT::w(i);
+      R = fmaf(w, qraw[i] - va_, R);
+      R = fmaf(w, qraw[i + 1] - vb_, R);
+    }
+    ENCODE_POP(0, d[0], p0_, v0_);
+    (void)v0_;
+    PopIO<ST>::st(p0_, fmaf(R, (float)(1.0 / LAT::w(0)), qraw[0]));
+  } else {
   // rest population: cu = cF = 0
   {
     ENCODE_POP(0, fmaf(om1, d[0], fmaf(omega_s, fmaf(M0, m15usq, dM), m3uF_s)), p0_, v0_);
@@ -479,6 +538,7 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
     ENCODE_POP(i + 1, fmaf(om1, d[i + 1], A - B), pb_, vb_);
     store_pop_pair<ST>(pa_, va_, pb_, vb_, rng, sr);
   }
+  }
 #undef ENCODE_POP
 #undef EPS_AT
 #undef DEPS_AT
@@ -501,22 +561,84 @@ __device__ __forceinline__ bool mbar_wait_or_abort(unsigned long long *bar, unsi
   return false;
 }
 
-// Warp-specialised row kernel.  The last warp is the producer: it
+// Bulk copy of `bytes` from shared to global memory (both 16-byte aligned, a
+// multiple of 16 bytes), tracked in this thread's bulk async-group.
+__device__ __forceinline__ void bulk_s2g(void *dst, const void *src, unsigned bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// wait until this thread's bulk stores have read their shared-memory source
+__device__ __forceinline__ void bulk_wait_read_all() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+// wait until this thread's bulk stores have completed
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// make this thread's shared-memory writes visible to the bulk-copy engine
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Shape of one row kernel instantiation.  FP16 rows are written back
+// through two output stages in shared memory by bulk copies (fewer
+// instructions per cell than scattered 2-byte stores: measured -8 % on the
+// odd step, +2 % GLUPS at 256^3), where that fits with at least two input
+// stages; FP32 keeps three input stages and stores directly (with output
+// staging it would drop to two input stages: measured 0.78 instead of 0.88
+// of the copy bandwidth).
+template <class LAT, class ST, int P, int MINB>
+struct RowCfg {
+  static constexpr int kIn = RowLayout<LAT, ST, true, P>::kStageBytes;  // the odd step's (larger) stage
+  static constexpr int kOut = (LAT::Q * P * (int)sizeof(ST) + 127) / 128 * 128;
+  static constexpr int kBudget = MINB > 1 ? 110 * 1024 : 216 * 1024;
+  static constexpr int kMaxIn = MINB > 1 ? 3 : 6;
+  static constexpr int kInWithOut = (kBudget - 2 * kOut) / kIn;
+  static constexpr bool kOuts = sizeof(ST) == 2 && kInWithOut >= 2;
+  static constexpr int kInOnly = kBudget / kIn;
+  static constexpr int kNS = kOuts ? (kInWithOut < kMaxIn ? kInWithOut : kMaxIn) : (kInOnly < kMaxIn ? kInOnly : kMaxIn);
+  static constexpr int kNOut = kOuts ? 2 : 0;
+  static constexpr int kConsumers = row_consumers<MINB>();
+  static constexpr int kThreads = (kConsumers + (kOuts ? 2 : 1)) * 32;
+  static constexpr int kSmem = kNS * kIn + kNOut * kOut;
+};
+
+// Warp-specialised row kernel.  Warp kConsumerWarps is the producer: it
 // stages row j into stage j % NSTAGE once the consumers have released the
 // row that used it before (empty barrier), arming the full barrier with the
 // byte count of the copies.  Each producer lane owns two of the row's copies,
 // set up once per launch, so staging a row costs a few instructions per lane
 // besides the copies.  The consumer warps wait on the full barrier, update
-// their cells and release the stage, one arrival per warp.  No block-wide
+// their cells and release the stage, one arrival per warp.
+// NOUT > 0: the consumers write the updated row into output stage j % NOUT
+// (after the storer has released it: oempty), then arrive on ofull; the
+// storer warp (kConsumerWarps + 1) waits on ofull, copies the Q output rows
+// to their destination rows with bulk copies (lane i: population i), waits
+// until the copies have read the stage and releases it.  No block-wide
 // barrier is taken inside the loop.
-template <class LAT, class ST, bool ODD, bool RED, bool WALLS, int PITCH, int NSTAGE, int MINB, int RS>
-__global__ void __launch_bounds__(row_threads<MINB>(), MINB) step_row_kernel(const LatticeDev *__restrict__ Lp, int k) {
-  constexpr int kConsumerWarps = row_consumers<MINB>();
+// TUNED = false: row_consumers<MINB>() consumer warps and MAXSTAGE input
+// stages, compile-time constants (the default shape).  TUNED = true: the
+// launch chooses the consumer warps (blockDim.x / 32 minus the producer and
+// storer warps, at most row_consumers<MINB>()) and the input stages
+// `nstage` (2 <= nstage <= MAXSTAGE), the autotuner's knobs; this generic
+// form costs 2-5 % at the default shape (measured), so it runs only when a
+// tuned shape differs from the default, and only for plain steps.
+template <class LAT, class ST, bool ODD, bool RED, bool WALLS, int PITCH, int MAXSTAGE, int MINB, int RS, int NOUT,
+          bool TUNED = false>
+__global__ void __launch_bounds__((row_consumers<MINB>() + (NOUT ? 2 : 1)) * 32, MINB)
+    step_row_kernel(const LatticeDev *__restrict__ Lp, int k, int nstage) {
+  constexpr int Q = LAT::Q;
   using Lay = RowLayout<LAT, ST, ODD, PITCH>;
+  constexpr int kOutBytes = (Q * PITCH * (int)sizeof(ST) + 127) / 128 * 128;
+  const int kConsumerWarps = TUNED ? (int)(blockDim.x >> 5) - (NOUT ? 2 : 1) : row_consumers<MINB>();
+  const int NSTAGE = TUNED ? nstage : MAXSTAGE;
+  const int kInRegion = NSTAGE * RowLayout<LAT, ST, true, PITCH>::kStageBytes;
   __shared__ LatticeDev Ls;
-  __shared__ alignas(8) unsigned long long full[NSTAGE];
-  __shared__ alignas(8) unsigned long long empty[NSTAGE];
-  __shared__ RowCtx ctx[NSTAGE];
+  __shared__ alignas(8) unsigned long long full[MAXSTAGE];
+  __shared__ alignas(8) unsigned long long empty[MAXSTAGE];
+  __shared__ alignas(8) unsigned long long ofull[NOUT > 0 ? NOUT : 1];
+  __shared__ alignas(8) unsigned long long oempty[NOUT > 0 ? NOUT : 1];
+  __shared__ RowCtx ctx[MAXSTAGE];
   __shared__ volatile int abort_flag;
   extern __shared__ __align__(128) unsigned char stages[];
   const int tid = threadIdx.x;
@@ -530,6 +652,10 @@ __global__ void __launch_bounds__(row_threads<MINB>(), MINB) step_row_kernel(con
     for (int s = 0; s < NSTAGE; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], kConsumerWarps);
+    }
+    for (int o = 0; o < NOUT; ++o) {
+      mbar_init(&ofull[o], kConsumerWarps);
+      mbar_init(&oempty[o], 1);
     }
     abort_flag = 0;
     mbar_fence_init();
@@ -600,6 +726,50 @@ __global__ void __launch_bounds__(row_threads<MINB>(), MINB) step_row_kernel(con
       for (int jj = issued_upto - NSTAGE + 1; jj <= issued_upto; ++jj)
         if (jj >= 0) mbar_wait_bounded(&full[jj % NSTAGE], (unsigned)((jj / NSTAGE) & 1));
     }
+  } else if (NOUT > 0 && warp == kConsumerWarps + 1) {
+    // ---------------- storer warp: lane i writes population i's row back
+    const int ny = L.ny, nz = L.nz, nxp = L.nxp;
+    const unsigned walls = L.walls;
+    const long long plane_bytes = L.plane * (long long)sizeof(ST);
+    const char *pop = static_cast<const char *>(L.pop);
+    const unsigned row_bytes = (unsigned)nxp * (unsigned)sizeof(ST);
+    int cy = 0, cz = 0;
+    if (lane < Q) dir_yz<LAT>(lane, cy, cz);
+    const bool moves = ODD && lane != 0;
+    const int step_y = (int)(gridDim.x % (unsigned)nyf), step_z = (int)(gridDim.x / (unsigned)nyf);
+    int ry = (int)(blockIdx.x % (unsigned)nyf), rz = (int)(blockIdx.x / (unsigned)nyf);
+    int j = 0;
+    for (int r = blockIdx.x; r < nrows; r += gridDim.x, ++j) {
+      const int o = j % NOUT;
+      if (!mbar_wait_or_abort(&ofull[o], (unsigned)((j / NOUT) & 1), limit, &abort_flag)) {
+        if (lane == 0 && !abort_flag) {
+          abort_flag = 1;
+          atomicExch(L.status, 1);
+        }
+        break;
+      }
+      const int y = y0 + ry, z = z0 + rz;
+      if (lane < Q) {
+        // even step, rest population, or a target row in a wall layer: the
+        // own row, plane opp(i); else plane i of row (y + c_iy, z + c_iz)
+        const bool to_nb = moves && !(walls && wall_row(walls, y + cy, z + cz, ny, nz));
+        const int yy = to_nb ? wrapi(y + cy, ny) : y, zz = to_nb ? wrapi(z + cz, nz) : z;
+        const int pl = to_nb ? lane : opp_of(lane);
+        char *dst = const_cast<char *>(pop) + pl * plane_bytes + (long long)((zz * ny + yy) * nxp) * sizeof(ST);
+        bulk_s2g(dst, stages + kInRegion + o * kOutBytes + lane * PITCH * (int)sizeof(ST), row_bytes);
+        bulk_commit();
+        bulk_wait_read_all();
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&oempty[o]);
+      ry += step_y;
+      rz += step_z;
+      if (ry >= nyf) {
+        ry -= nyf;
+        ++rz;
+      }
+    }
+    if (lane < Q) bulk_wait_all();
   } else {
     // ---------------- consumer warps
     const long long n = L.n + k;
@@ -615,15 +785,32 @@ __global__ void __launch_bounds__(row_threads<MINB>(), MINB) step_row_kernel(con
         }
         break;
       }
+      unsigned char *ostage = nullptr;
+      if (NOUT > 0) {
+        const int o = j % NOUT;
+        // the storer has finished reading row j - NOUT from this output stage
+        if (j >= NOUT && !mbar_wait_or_abort(&oempty[o], (unsigned)(((j / NOUT) - 1) & 1), limit, &abort_flag)) {
+          if (lane == 0 && !abort_flag) {
+            abort_flag = 1;
+            atomicExch(L.status, 1);
+          }
+          break;
+        }
+        ostage = stages + kInRegion + o * kOutBytes;
+      }
       // 32-cell chunks of the row, dealt round-robin to the consumer warps
       // across rows so that every warp gets the same share
       const int nchunks = (L.nx + 31) >> 5;
       const int first = (warp - (int)(((long long)j * nchunks) % kConsumerWarps) + kConsumerWarps) % kConsumerWarps;
       for (int c = first; c < nchunks; c += kConsumerWarps)
-        update_row_chunk<LAT, ST, ODD, RED, WALLS, PITCH, RS>(L, stages + s * Lay::kStageBytes, ctx[s], n, dn,
-                                                          dn_force, (c << 5) + lane, acc);
+        update_row_chunk<LAT, ST, ODD, RED, WALLS, PITCH, RS, (NOUT > 0)>(
+            L, stages + s * Lay::kStageBytes, ctx[s], n, dn, dn_force, (c << 5) + lane, acc, ostage);
+      if (NOUT > 0) fence_proxy_async_smem();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[s]);
+      if (lane == 0) {
+        mbar_arrive(&empty[s]);
+        if (NOUT > 0) mbar_arrive(&ofull[j % NOUT]);
+      }
     }
   }
   __syncthreads();
@@ -637,32 +824,31 @@ namespace lbm {
 // Host side: launch and planning of the row kernel for one lattice type.
 // ls.row encodes the variant: bit 0 set = in use, bit 1 = walls, bit 2 =
 // pitch 512 (else 256).
-#ifndef LBM_ROW_NSTAGE_256
-#define LBM_ROW_NSTAGE_256 3
-#endif
-// Stages per block: 3 at two blocks per SM; with one block per SM as many as
-// fit in 216 KB, at most 6.
-template <class LAT, class ST, int P, int MINB>
-constexpr int row_stages() {
-  return MINB > 1 ? LBM_ROW_NSTAGE_256
-                  : (216 * 1024 / RowLayout<LAT, ST, true, P>::kStageBytes > 6
-                         ? 6
-                         : 216 * 1024 / RowLayout<LAT, ST, true, P>::kStageBytes);
-}
-
 template <class LAT, class ST, bool W, int P, int MINB, int RS>
 cudaError_t launch_row_rs(const LatticeDev *L_dev, bool odd, bool red, int k, const StepLaunch &ls,
                           cudaStream_t s) {
-  constexpr int NS = row_stages<LAT, ST, P, MINB>();
-  const dim3 grid(ls.row_grid), block(row_threads<MINB>());
+  using C = RowCfg<LAT, ST, P, MINB>;
+  constexpr int NS = C::kNS, NO = C::kNOut;
+  // a tuned shape (row_consumers, row_stages) other than the default runs the
+  // generic instantiation, for plain steps only
+  const int nc = ls.row_consumers > 0 && ls.row_consumers <= C::kConsumers ? ls.row_consumers : C::kConsumers;
+  const int ns = ls.row_stages >= 2 && ls.row_stages <= NS ? ls.row_stages : NS;
+  const dim3 grid(ls.row_grid);
+  if (RS == 0 && !red && (nc != C::kConsumers || ns != NS)) {
+    const dim3 block((nc + (NO ? 2 : 1)) * 32);
+    const int smem = ns * C::kIn + NO * C::kOut;
+    if (odd) step_row_kernel<LAT, ST, true, false, W, P, NS, MINB, RS, NO, true><<<grid, block, smem, s>>>(L_dev, k, ns);
+    else step_row_kernel<LAT, ST, false, false, W, P, NS, MINB, RS, NO, true><<<grid, block, smem, s>>>(L_dev, k, ns);
+    return cudaGetLastError();
+  }
+  const dim3 block(C::kThreads);
+  const int smem = C::kSmem;
   if (odd) {
-    const int smem = RowLayout<LAT, ST, true, P>::kStageBytes * NS;
-    if (red) step_row_kernel<LAT, ST, true, true, W, P, NS, MINB, RS><<<grid, block, smem, s>>>(L_dev, k);
-    else step_row_kernel<LAT, ST, true, false, W, P, NS, MINB, RS><<<grid, block, smem, s>>>(L_dev, k);
+    if (red) step_row_kernel<LAT, ST, true, true, W, P, NS, MINB, RS, NO><<<grid, block, smem, s>>>(L_dev, k, ns);
+    else step_row_kernel<LAT, ST, true, false, W, P, NS, MINB, RS, NO><<<grid, block, smem, s>>>(L_dev, k, ns);
   } else {
-    const int smem = RowLayout<LAT, ST, false, P>::kStageBytes * NS;
-    if (red) step_row_kernel<LAT, ST, false, true, W, P, NS, MINB, RS><<<grid, block, smem, s>>>(L_dev, k);
-    else step_row_kernel<LAT, ST, false, false, W, P, NS, MINB, RS><<<grid, block, smem, s>>>(L_dev, k);
+    if (red) step_row_kernel<LAT, ST, false, true, W, P, NS, MINB, RS, NO><<<grid, block, smem, s>>>(L_dev, k, ns);
+    else step_row_kernel<LAT, ST, false, false, W, P, NS, MINB, RS, NO><<<grid, block, smem, s>>>(L_dev, k, ns);
   }
   return cudaGetLastError();
 }
@@ -688,22 +874,24 @@ cudaError_t launch_row_t(const LatticeDev *L_dev, bool odd, int red, int k, cons
   return launch_row_v<LAT, ST, false, 256, MINB>(L_dev, odd, red, k, ls, s);
 }
 
-template <class LAT, class ST, bool W, int P, int MINB, bool ODD, bool RED, int RS>
+template <class LAT, class ST, bool W, int P, int MINB, bool ODD, bool RED, int RS, bool TUNED = false>
 cudaError_t configure_row_one(int smem) {
-  constexpr int NS = row_stages<LAT, ST, P, MINB>();
-  return cudaFuncSetAttribute(step_row_kernel<LAT, ST, ODD, RED, W, P, NS, MINB, RS>,
+  using C = RowCfg<LAT, ST, P, MINB>;
+  return cudaFuncSetAttribute(step_row_kernel<LAT, ST, ODD, RED, W, P, C::kNS, MINB, RS, C::kNOut, TUNED>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
 template <class LAT, class ST, bool W, int P, int MINB>
-int configure_row_v(int &occ) {
-  constexpr int NS = row_stages<LAT, ST, P, MINB>();
-  static_assert(NS >= 2, "a row kernel needs at least two stages");
-  const int smem = RowLayout<LAT, ST, true, P>::kStageBytes * NS;
-  if (smem > 220 * 1024) return 0;
+int configure_row_v(int &occ, int &nc, int &ns) {
+  using C = RowCfg<LAT, ST, P, MINB>;
+  static_assert(C::kNS >= 2, "a row kernel needs at least two stages");
+  nc = nc > 0 && nc <= C::kConsumers ? nc : C::kConsumers;
+  ns = ns >= 2 && ns <= C::kNS ? ns : C::kNS;
+  const int smem_max = C::kSmem;
+  if (smem_max > 220 * 1024) return 0;
   cudaError_t e = cudaSuccess;
 #define LBM_CFG(ODD, RED, RS) \
-  if (e == cudaSuccess) e = configure_row_one<LAT, ST, W, P, MINB, ODD, RED, RS>(smem)
+  if (e == cudaSuccess) e = configure_row_one<LAT, ST, W, P, MINB, ODD, RED, RS>(smem_max)
   LBM_CFG(true, false, 0);
   LBM_CFG(true, true, 0);
   LBM_CFG(false, false, 0);
@@ -713,9 +901,16 @@ int configure_row_v(int &occ) {
   LBM_CFG(false, false, 1);
   LBM_CFG(false, true, 1);
 #undef LBM_CFG
+  if (e == cudaSuccess) e = configure_row_one<LAT, ST, W, P, MINB, true, false, 0, true>(smem_max);
+  if (e == cudaSuccess) e = configure_row_one<LAT, ST, W, P, MINB, false, false, 0, true>(smem_max);
+  const int threads = (nc + (C::kNOut ? 2 : 1)) * 32;
+  const int smem = ns * C::kIn + C::kNOut * C::kOut;
+  const bool tuned = nc != C::kConsumers || ns != C::kNS;
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &occ, step_row_kernel<LAT, ST, true, false, W, P, NS, MINB, 0>, row_threads<MINB>(), smem);
+    e = tuned ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &occ, step_row_kernel<LAT, ST, true, false, W, P, C::kNS, MINB, 0, C::kNOut, true>, threads, smem)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &occ, step_row_kernel<LAT, ST, true, false, W, P, C::kNS, MINB, 0, C::kNOut>, threads, smem);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -729,13 +924,16 @@ int plan_row_t(int nx, int nxp, int ny, int nz, unsigned walls, StepLaunch &ls) 
   if ((long long)nxp * ny * nz > 0x7fffffffLL) return 0;  // int cell indices
   if (walls & 1u) return 0;
   const bool w = (walls & 6u) != 0, p512 = nxp > 256;
-  int occ = 0, ok;
+  int occ = 0, ok, nc = ls.row_consumers, ns = ls.row_stages;
   if (p512)
-    ok = w ? configure_row_v<LAT, ST, true, 512, (MINB > 1 ? MINB - 1 : 1)>(occ)
-           : configure_row_v<LAT, ST, false, 512, (MINB > 1 ? MINB - 1 : 1)>(occ);
+    ok = w ? configure_row_v<LAT, ST, true, 512, (MINB > 1 ? MINB - 1 : 1)>(occ, nc, ns)
+           : configure_row_v<LAT, ST, false, 512, (MINB > 1 ? MINB - 1 : 1)>(occ, nc, ns);
   else
-    ok = w ? configure_row_v<LAT, ST, true, 256, MINB>(occ) : configure_row_v<LAT, ST, false, 256, MINB>(occ);
+    ok = w ? configure_row_v<LAT, ST, true, 256, MINB>(occ, nc, ns)
+           : configure_row_v<LAT, ST, false, 256, MINB>(occ, nc, ns);
   if (!ok) return 0;
+  ls.row_consumers = nc;
+  ls.row_stages = ns;
   const int nyf = (walls & 2u) ? ny - 2 : ny;
   const int nzf = (walls & 4u) ? nz - 2 : nz;
   const int nrows = nyf * nzf;

@@ -32,6 +32,16 @@ MASTER_SEED = 20220819
 CS2 = 1.0 / 3.0
 
 
+def _xp(a):
+    """numpy, or torch when `a` is a torch tensor (the manufactured fields
+    below are evaluated with either, so that the GPU tests can generate them
+    on the device)."""
+    if type(a).__module__.startswith("torch"):
+        import torch
+        return torch
+    return np
+
+
 def rng(offset: int = 0) -> np.random.Generator:
     return np.random.default_rng(MASTER_SEED + int(offset))
 
@@ -227,7 +237,7 @@ class MMS:
     # analytic fields, X = (x, y, z) in metres, t in seconds
     def eps(self, X, t):
         x, y, z = X
-        s = np.sin
+        s = _xp(x).sin
         pi = np.pi
         e = self.example
         if e == 1:
@@ -242,7 +252,8 @@ class MMS:
 
     def u(self, X, t):
         x, y, z = X
-        s, c, pi = np.sin, np.cos, np.pi
+        xp = _xp(x)
+        s, c, pi = xp.sin, xp.cos, np.pi
         e = self.example
         zero = 0.0 * x
         if e == 1:
@@ -261,7 +272,7 @@ class MMS:
 
     def p(self, X, t):
         x, y, z = X
-        s, pi = np.sin, np.pi
+        s, pi = _xp(x).sin, np.pi
         e = self.example
         if e == 1:
             return s(pi * x) * s(pi * y)
@@ -323,9 +334,10 @@ class MMS:
             raise ValueError("closed form only for the transient examples")
         axes = list(range(self.dim))
         pi = np.pi
+        xp = _xp(X[0])
         xi = [X[k] - 0.5 * t for k in axes]
-        sn = [np.sin(pi * v) for v in xi]
-        cs = [np.cos(pi * v) for v in xi]
+        sn = [xp.sin(pi * v) for v in xi]
+        cs = [xp.cos(pi * v) for v in xi]
 
         def prod_except(skip):
             out = 1.0
@@ -367,6 +379,22 @@ class MMS:
         F = np.stack(self.force_closed(Xt, tt), axis=1).reshape(nsteps, 3, -1)
         return np.ascontiguousarray(eps), np.ascontiguousarray(F * self.dt * self.dt / self.dx)
 
+    def lattice_series_torch(self, n0: int, nsteps: int, device="cuda", dtype=None):
+        """lattice_series evaluated with torch on `device`: the exact per-step
+        phi (nsteps, N) and F_MMS (nsteps, 3, N) of a transient example,
+        generated where the solver reads them."""
+        import torch
+        dtype = dtype or torch.float64
+        X = [torch.as_tensor(c, dtype=torch.float64, device=device) for c in self.coords()]
+        t = (n0 + torch.arange(nsteps, dtype=torch.float64, device=device)) * self.dt
+        Xt = [c.unsqueeze(0).expand((nsteps,) + tuple(c.shape)) for c in X]
+        tt = t.reshape(nsteps, 1, 1, 1)
+        eps = self.eps(Xt, tt).reshape(nsteps, -1)
+        F = torch.stack([f.expand((nsteps,) + tuple(X[0].shape)) if torch.is_tensor(f) else f
+                         for f in self.force_closed(Xt, tt)], dim=1).reshape(nsteps, 3, -1)
+        F = F * (self.dt * self.dt / self.dx)
+        return eps.to(dtype).contiguous(), F.to(dtype).contiguous()
+
     # lattice-unit views at time step n
     def lattice_fields(self, n: int):
         """dict(eps, deps_dt, force, dforce_dt, u, p) in lattice units at step n
@@ -382,12 +410,13 @@ class MMS:
         deps = _d(self.eps, 3, self.h_fd * 1e-2)(X, t) * dt
         force = self.force if self.stationary else self.force_closed
         F = np.stack(force(X, t)) * dt * dt / dx
-        dF = np.stack(_d(lambda Y, s: np.stack(force(Y, s)), 3, 1e-4)(X, t)) * dt * dt / dx * dt
+        dF = None
+        if not self.stationary:
+            dF = np.stack(_d(lambda Y, s: np.stack(force(Y, s)), 3, 1e-4)(X, t)) * dt * dt / dx * dt
         u = np.stack(self.u(X, t)) * dt / dx
         p = self.p(X, t) * dt * dt / (dx * dx)
         return {"eps": eps, "deps_dt": deps if not self.stationary else None,
-                "force": F, "dforce_dt": dF if not self.stationary else None,
-                "u": u, "p": p}
+                "force": F, "dforce_dt": dF, "u": u, "p": p}
 
     def steps_for(self, t_end: float) -> int:
         return int(round(t_end / self.dt))
@@ -462,10 +491,13 @@ def poisson_requests(rate: float, count: int, seed_offset: int = 5000,
     or (half of them) a steady-state residual target of 1e-8 with that budget
     as the cap.  Returns [(arrival_s, LatticeSpec)]."""
     g = rng(seed_offset)
+    # arrival times from a stream of their own: the same seed gives the same
+    # sequence of problems at every rate
+    g_arrival = rng(seed_offset + 1_000_003)
     t = 0.0
     out = []
     for j in range(count):
-        t += float(g.exponential(1.0 / rate))
+        t += float(g_arrival.exponential(1.0 / rate))
         side = int(round(math.exp(g.uniform(math.log(sides[0]), math.log(sides[1])))))
         nsteps = int(round(math.exp(g.uniform(math.log(steps[0]), math.log(steps[1])))))
         kind = "spheres" if g.uniform() < sphere_share else "sine"
@@ -475,3 +507,15 @@ def poisson_requests(rate: float, count: int, seed_offset: int = 5000,
                            steps=nsteps, residual_tol=tol)
         out.append((t, spec))
     return out
+
+
+_EPS_CACHE = {}
+
+
+def cached_eps(spec) -> np.ndarray:
+    """spec.eps() as float32, kept for reuse (the same problem served at
+    several arrival rates is generated once)."""
+    key = (spec.kind, spec.shape, spec.amp, spec.seed)
+    if key not in _EPS_CACHE:
+        _EPS_CACHE[key] = spec.eps().astype(np.float32).ravel()
+    return _EPS_CACHE[key]

@@ -15,10 +15,10 @@ import numpy as np
 
 from . import build as _build
 
-LATTICES = {"D2Q9": 0, "D3Q19": 1, "D3Q27": 2}
+LATTICES = {"D2Q9": 0, "D3Q19": 1, "D3Q27": 2, "D1Q3": 3}
 STORAGES = {"fp64": 0, "fp32": 1, "fp16": 2}
-Q_OF = {0: 9, 1: 19, 2: 27}
-DIM_OF = {0: 2, 1: 3, 2: 3}
+Q_OF = {0: 9, 1: 19, 2: 27, 3: 3}
+DIM_OF = {0: 2, 1: 3, 2: 3, 3: 1}
 STATUS = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA",
           -4: "LBM_EUNSTABLE", -5: "LBM_ETIMEOUT", -6: "LBM_ESTATE"}
 
@@ -41,7 +41,10 @@ class Params(ctypes.Structure):
         ("walls", ctypes.c_uint), ("fp16_scale_log2", ctypes.c_int),
         ("cuda_stream", ctypes.c_void_p), ("hbm_budget_bytes", ctypes.c_size_t),
         ("block_x", ctypes.c_int), ("block_y", ctypes.c_int), ("kernel", ctypes.c_int),
-        ("fp16_rounding", ctypes.c_int),
+        ("fp16_rounding", ctypes.c_int), ("quad_auto", ctypes.c_int),
+        ("drag_model", ctypes.c_int), ("drag_c1", ctypes.c_double), ("drag_c2", ctypes.c_double),
+        ("drag_d", ctypes.c_double), ("les_cs", ctypes.c_double),
+        ("row_consumers", ctypes.c_int), ("row_stages", ctypes.c_int),
     ]
 
 
@@ -89,6 +92,7 @@ _SIGS = {
     "lbm_vanse_launch_count": (ctypes.c_longlong, []),
     "lbm_vanse_set_wait_limit": (ctypes.c_int, [_H, ctypes.c_uint, ctypes.c_int]),
     "lbm_vanse_uses_row_kernel": (ctypes.c_int, [_H]),
+    "lbm_vanse_launch_shape": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int * 4)]),
     "lbm_vanse_get_params": (ctypes.c_int, [_H, ctypes.POINTER(Params)]),
     "lbm_vanse_save_state": (ctypes.c_int, [_H, _P, ctypes.POINTER(ctypes.c_size_t)]),
     "lbm_vanse_load_state": (ctypes.c_int, [_H, _P, ctypes.c_size_t]),
@@ -187,16 +191,38 @@ class Lattice:
 
     def __init__(self, lattice="D3Q19", shape=(32, 32, 32), tau=0.6, storage="fp32", rho0=1.0,
                  quad_axes=0, quad_dim=0, walls=0, fp16_scale_log2=10, stream=None,
-                 hbm_budget_bytes=0, block=(0, 0), kernel=0, fp16_rounding="stochastic"):
-        """shape is (nx, ny, nz); nz = 1 for D2Q9."""
+                 hbm_budget_bytes=0, block=(0, 0), kernel=0, fp16_rounding="stochastic",
+                 drag=None, les_cs=0.0, row_shape=None, tuned=True):
+        """shape is (nx, ny, nz); nz = 1 for D2Q9, ny = nz = 1 for D1Q3.
+        quad_axes: an axis bitmask, 0 (every axis) or "auto" (chosen from
+        phi at every refresh).  drag: None or (c1, c2, d) of the Ergun-type
+        drag law; les_cs: Smagorinsky constant (0 = BGK).  row_shape:
+        (consumer warps, staged rows) of the row-staged kernel, or None.
+        tuned: when kernel, block and row_shape are left at their defaults,
+        take them from the autotuner's cache for this size bucket (tune.py),
+        if it holds an entry."""
         L = lib()
         p = Params()
         _check(L.lbm_vanse_params_default(ctypes.byref(p)))
+        self.tuned_from = None
+        if tuned and kernel in (0, "auto") and tuple(block) == (0, 0) and row_shape is None:
+            from . import tune
+            hit = tune.best_config(lattice if isinstance(lattice, str) else
+                                   {v: k for k, v in LATTICES.items()}[int(lattice)],
+                                   storage if isinstance(storage, str) else
+                                   {v: k for k, v in STORAGES.items()}[int(storage)], shape)
+            if hit is not None:
+                kernel, block, row_shape = hit["kernel"], tuple(hit["block"]), hit.get("row_shape")
+                self.tuned_from = hit.get("key")
         p.lattice = LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
         p.storage = STORAGES[storage] if isinstance(storage, str) else int(storage)
         nx, ny, nz = (list(shape) + [1, 1])[:3]
         p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
         p.tau, p.rho0 = float(tau), float(rho0)
+        if isinstance(quad_axes, str):
+            if quad_axes != "auto":
+                raise ValueError('quad_axes: an axis bitmask or "auto"')
+            p.quad_auto, quad_axes = 1, 0
         p.quad_axes, p.quad_dim, p.walls = int(quad_axes), int(quad_dim), int(walls)
         p.fp16_scale_log2 = int(fp16_scale_log2)
         p.cuda_stream = stream
@@ -204,6 +230,12 @@ class Lattice:
         p.block_x, p.block_y = int(block[0]), int(block[1])
         p.kernel = {"auto": 0, "cell": 1, "row": 2}.get(kernel, kernel)
         p.fp16_rounding = {"stochastic": 0, "nearest": 1}.get(fp16_rounding, fp16_rounding)
+        if row_shape is not None:
+            p.row_consumers, p.row_stages = (int(v) for v in row_shape)
+        if drag is not None:
+            p.drag_model = 1
+            p.drag_c1, p.drag_c2, p.drag_d = (float(v) for v in drag)
+        p.les_cs = float(les_cs)
         h = ctypes.c_void_p()
         _check(L.lbm_vanse_create(ctypes.byref(p), ctypes.byref(h)))
         self._h = h
@@ -299,6 +331,26 @@ class Lattice:
         return st.as_dict()
 
     @property
+    def quadrature(self):
+        """(quad_axes, quad_dim) in use: the axes of eq. (quad) and the row
+        of Table "weights" (chosen from phi when created with
+        quad_axes="auto")."""
+        p = Params()
+        _check(lib().lbm_vanse_get_params(self.handle, ctypes.byref(p)), self.handle)
+        return int(p.quad_axes), int(p.quad_dim)
+
+    @property
+    def launch_shape(self) -> dict:
+        """The step's launch shape (kernel and, for the row-staged kernel,
+        consumer warps, staged rows and grid)."""
+        a = (ctypes.c_int * 4)()
+        _check(lib().lbm_vanse_launch_shape(self.handle, ctypes.byref(a)), self.handle)
+        kern = {0: "fp64-cell", 1: "cell", 2: "row"}[a[0]]
+        if a[0] == 2:
+            return {"kernel": kern, "consumers": a[1], "stages": a[2], "grid": a[3]}
+        return {"kernel": kern, "block": [a[1], a[2]], "grid": a[3]}
+
+    @property
     def row_kernel(self) -> bool:
         return lib().lbm_vanse_uses_row_kernel(self.handle) == 1
 
@@ -387,7 +439,17 @@ class Batch:
     """Many lattices advanced together (lbm_vanse_batch_t): one persistent,
     graph-captured kernel per (lattice, storage) type per step."""
 
-    def __init__(self, max_members=256, max_tiles=65536, tile_cells=0, stream=None):
+    def __init__(self, max_members=256, max_tiles=65536, tile_cells=None, stream=None, storage="fp16"):
+        """tile_cells: cells per tile of the one-cell-per-thread batch kernel;
+        None = the autotuner's cached choice for this storage, else the
+        library default."""
+        self.tuned_from = None
+        if tile_cells is None:
+            from . import tune
+            hit = tune.best_tile(storage)
+            tile_cells = hit["best"] if hit else 0
+            self.tuned_from = hit["key"] if hit else None
+        self.tile_cells = int(tile_cells)
         h = ctypes.c_void_p()
         _check(lib().lbm_vanse_batch_create(int(max_members), int(max_tiles), int(tile_cells),
                                             stream, ctypes.byref(h)))

@@ -71,6 +71,7 @@ class ServerStats:
     macro_steps: int = 0
     peak_members: int = 0
     peak_bytes: int = 0
+    incomplete: int = 0
 
     def summary(self) -> dict:
         lat = np.array(self.latencies) if self.latencies else np.array([np.nan])
@@ -81,7 +82,8 @@ class ServerStats:
                 "p99_latency_s": float(np.percentile(lat, 99)),
                 "mean_latency_s": float(np.mean(lat)),
                 "elapsed_s": self.elapsed, "macro_steps": self.macro_steps,
-                "peak_members": self.peak_members, "peak_bytes": self.peak_bytes}
+                "peak_members": self.peak_members, "peak_bytes": self.peak_bytes,
+                "incomplete": self.incomplete}
 
 
 class Server:
@@ -93,7 +95,7 @@ class Server:
     finished request to the host."""
 
     def __init__(self, storage="fp16", hbm_budget=80e9, macro_steps=100, max_members=1024,
-                 max_tiles=1 << 20, tile_cells=0, stream=None, keep_results=True,
+                 max_tiles=1 << 20, tile_cells=None, stream=None, keep_results=True,
                  fp16_scale_log2=10):
         if macro_steps < 2 or macro_steps % 2:
             raise ValueError("macro_steps must be even and >= 2")
@@ -104,7 +106,7 @@ class Server:
         self.keep_results = keep_results
         self.fp16_k = fp16_scale_log2
         self.batch = lbm.Batch(max_members=max_members, max_tiles=max_tiles,
-                               tile_cells=tile_cells, stream=stream)
+                               tile_cells=tile_cells, stream=stream, storage=storage)
         self.queue = deque()
         self.active: list[Request] = []
         self.done: list[Request] = []
@@ -156,7 +158,13 @@ class Server:
     def _retire(self, req: Request, now_fn, status: str):
         lat = req.lattice
         if self.keep_results:
-            m = lat.moments(f64=False)
+            # the read-back through the library's fixed staging array takes no
+            # device memory outside the admission budget (the server loop is
+            # single-threaded, so its calls never overlap)
+            if lat.n <= lbm.NOALLOC_MAX_CELLS:
+                m = lat.moments_noalloc()
+            else:
+                m = lat.moments(f64=False)
             req.result = {"u": m["u"], "p": m["p"]}
         req.finished = now_fn()
         req.status = status
@@ -191,6 +199,8 @@ class Server:
             self._retire(req, now_fn, status)
 
     def run(self, requests, timeout_s: float = 3600.0):
+        """(see below); requests still queued or running when timeout_s
+        passes are counted as incomplete."""
         """Serve a list of requests whose .arrival are seconds after the start
         (arrivals are simulated against the wall clock); returns the stats
         summary."""
@@ -215,6 +225,7 @@ class Server:
             if wait > 0:
                 time.sleep(min(wait, 0.05))
         self.stats.elapsed = now()
+        self.stats.incomplete = len(self.active) + len(self.queue)
         return self.stats.summary()
 
     def close(self):
@@ -225,15 +236,19 @@ class Server:
         self.batch.close()
 
 
-def run_sequential(requests, storage="fp32", check_every=100, stream=None, keep_results=True):
+def run_sequential(requests, storage="fp32", check_every=100, stream=None, keep_results=True,
+                   timeout_s: float = float("inf")):
     """The plain per-request baseline: one solver per request, first come
-    first served, each run to its step budget or residual target alone."""
+    first served, each run to its step budget or residual target alone.
+    Requests not started by timeout_s are left queued."""
     stats = ServerStats()
     t0 = time.perf_counter()
 
     def now():
         return time.perf_counter() - t0
     for req in sorted(requests, key=lambda r: r.arrival):
+        if now() > timeout_s:
+            break
         wait = req.arrival - now()
         if wait > 0:
             time.sleep(wait)
@@ -257,6 +272,7 @@ def run_sequential(requests, storage="fp32", check_every=100, stream=None, keep_
         stats.latencies.append(req.latency)
         stats.cell_updates += s.cells * req.steps_done
     stats.elapsed = now()
+    stats.incomplete = len(requests) - stats.completed
     return stats.summary()
 
 
@@ -264,8 +280,9 @@ def make_requests(rate: float, count: int, seed_offset: int = 5000, sides=(32, 1
                   steps=(500, 20000), residual_share=0.5, sphere_share=0.5, with_eps=True):
     """Poisson request trace with client-generated phi fields."""
     from .inputs import poisson_requests
+    from .inputs import cached_eps
     out = []
     for j, (t, spec) in enumerate(poisson_requests(rate, count, seed_offset, sides, steps,
                                                    residual_share, sphere_share)):
-        out.append(Request(j, spec, t, spec.eps() if with_eps else None))
+        out.append(Request(j, spec, t, cached_eps(spec) if with_eps else None))
     return out

@@ -23,6 +23,9 @@ BLOCK_CANDIDATES = [(32, 1), (32, 2), (32, 4), (32, 8), (64, 1), (64, 2), (64, 4
 TILE_CANDIDATES = [1024, 2048, 4096, 8192, 16384]
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build",
                              "autotune.json")
+# results of tuning runs on GB300 shipped with the package: read first, then
+# overlaid by the local cache (which every tuning run writes)
+SEED_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_gb300.json")
 _lock = threading.Lock()
 
 
@@ -32,16 +35,23 @@ def bucket_key(lattice: str, storage: str, shape) -> str:
     return f"{lattice}/{storage}/b{int(math.log2(max(cells, 1)))}/x{'32' if nx % 32 == 0 else 'r'}"
 
 
+def default_cache_path() -> str:
+    """LBM_TUNE_CACHE, else the package's build directory."""
+    return os.environ.get("LBM_TUNE_CACHE") or DEFAULT_CACHE
+
+
 class Cache:
-    def __init__(self, path: str = DEFAULT_CACHE):
+    def __init__(self, path: str | None = None, seed: str | None = SEED_CACHE):
+        path = path or default_cache_path()
         self.path = path
         self.data = {}
-        if os.path.exists(path):
-            try:
-                with open(path) as fh:
-                    self.data = json.load(fh)
-            except (OSError, ValueError):
-                self.data = {}
+        for f in ([seed] if seed else []) + [path]:
+            if os.path.exists(f):
+                try:
+                    with open(f) as fh:
+                        self.data.update(json.load(fh))
+                except (OSError, ValueError):
+                    pass
 
     def get(self, key):
         return self.data.get(key)
@@ -69,12 +79,19 @@ def _time_steps(lat, steps, warmup):
     return a.elapsed_time(b) / steps
 
 
+# (consumer warps, staged rows) of the row-staged kernel; shapes the
+# library cannot launch for a lattice type fall back to its default and are
+# recorded under the shape that ran
+ROW_SHAPES = [(0, 0), (5, 2), (5, 3), (6, 2), (6, 3), (7, 2), (7, 3), (11, 3), (13, 4), (15, 4)]
+
+
 def tune_step(lattice="D3Q19", storage="fp32", shape=(128, 128, 128), tau=0.6, steps=20, warmup=4,
-              cache: Cache | None = None, blocks=None, force=True):
-    """Time the row-staged kernel (when the lattice qualifies) and the
-    one-cell-per-thread kernel with each block shape on a lattice of this
-    size.  Caches and returns (best, timings): best = {"kernel": 1|2,
-    "block": [bx, by]}, timings in ms per step per candidate."""
+              cache: Cache | None = None, blocks=None, row_shapes=None, force=True):
+    """Time the row-staged kernel in each shape (consumer warps, staged
+    rows) when the lattice qualifies, and the one-cell-per-thread kernel
+    with each block shape, on a lattice of this size.  Caches and returns
+    (best, timings): best = {"kernel": 1|2, "block": [bx, by], "row_shape":
+    [consumers, stages] or None}, timings in ms per step per candidate."""
     import torch
     cache = cache or Cache()
     key = "step/" + bucket_key(lattice, storage, shape)
@@ -85,36 +102,60 @@ def tune_step(lattice="D3Q19", storage="fp32", shape=(128, 128, 128), tau=0.6, s
     nx, ny, nz = (list(shape) + [1, 1])[:3]
     timings, configs = {}, {}
 
-    def trial(name, kernel, block):
+    def trial(kernel, block, row_shape):
         try:
             lat = lbm.Lattice(lattice, (nx, ny, nz), tau=tau, storage=storage, stream=stream,
-                              block=block, kernel=kernel)
+                              block=block, kernel=kernel, row_shape=row_shape, tuned=False)
         except lbm.LbmError:
             return
-        lat.set_force((1e-6, 0, 0))
-        lat.init_equilibrium()
-        timings[name] = _time_steps(lat, steps, warmup)
-        configs[name] = {"kernel": kernel, "block": list(block)}
+        ls = lat.launch_shape
+        if ls["kernel"] == "row":
+            name = f"row{ls['consumers']}x{ls['stages']}"
+            cfg = {"kernel": 2, "block": [0, 0], "row_shape": [ls["consumers"], ls["stages"]]}
+        else:
+            name = f"cell{ls['block'][0]}x{ls['block'][1]}"
+            cfg = {"kernel": 1, "block": list(ls["block"]), "row_shape": None}
+        if name not in timings:
+            lat.set_force((1e-6, 0, 0))
+            lat.init_equilibrium()
+            timings[name] = _time_steps(lat, steps, warmup)
+            configs[name] = cfg
         lat.close()
     if storage != "fp64":
-        trial("row", 2, (0, 0))
+        for rs in row_shapes or ROW_SHAPES:
+            trial(2, (0, 0), rs)
     for bx, by in blocks or BLOCK_CANDIDATES:
         if by > ny or bx > 2 * max(nx, 32):
             continue
-        trial(f"cell{bx}x{by}", 1, (bx, by))
+        trial(1, (bx, by), None)
     best = min(timings, key=timings.get)
     cache.put(key, {"best": configs[best], "ms": timings, "shape": [nx, ny, nz]})
     return configs[best], timings
 
 
 def best_config(lattice, storage, shape, cache: Cache | None = None):
-    """Cached (kernel, block) for this size bucket, or the library default
-    (automatic kernel choice, default block)."""
+    """The cached launch configuration for this size bucket: a dict with
+    "kernel" (1 one cell per thread, 2 row-staged), "block" and "row_shape"
+    (consumer warps, staged rows), and "key", or None when the bucket has
+    not been tuned (the library then chooses)."""
     cache = cache or Cache()
-    hit = cache.get("step/" + bucket_key(lattice, storage, shape))
-    if hit:
-        return hit["best"]["kernel"], tuple(hit["best"]["block"])
-    return 0, (0, 0)
+    key = "step/" + bucket_key(lattice, storage, shape)
+    hit = cache.get(key)
+    if not hit:
+        return None
+    out = dict(hit["best"])
+    out["key"] = key
+    return out
+
+
+def best_tile(storage, cache: Cache | None = None):
+    """The cached tile size of the one-cell-per-thread batch kernel for this
+    storage ({"best": cells, "key": ...}), or None."""
+    cache = cache or Cache()
+    keys = sorted(k for k in cache.data if k.startswith(f"tile/{storage}/"))
+    if not keys:
+        return None
+    return {"best": cache.data[keys[-1]]["best"], "key": keys[-1]}
 
 
 def tune_block(lattice="D3Q19", storage="fp32", shape=(128, 128, 128), tau=0.6, steps=20,
@@ -134,7 +175,7 @@ def tune_block(lattice="D3Q19", storage="fp32", shape=(128, 128, 128), tau=0.6, 
         if by > ny or bx > 2 * max(nx, 32):
             continue
         lat = lbm.Lattice(lattice, (nx, ny, nz), tau=tau, storage=storage, stream=stream,
-                          block=(bx, by), kernel="cell")
+                          block=(bx, by), kernel="cell", tuned=False)
         if eps is not None:
             lat.set_epsilon(eps)
         lat.set_force((1e-6, 0, 0))
@@ -168,7 +209,8 @@ def tune_tiles(specs, storage="fp16", steps=10, candidates=None, cache: Cache | 
     lats = []
     for s in specs:
         nz, ny, nx = s.shape
-        lat = lbm.Lattice(s.lattice, (nx, ny, nz), tau=s.tau, storage=storage, stream=stream)
+        lat = lbm.Lattice(s.lattice, (nx, ny, nz), tau=s.tau, storage=storage, stream=stream,
+                          tuned=False)
         lat.set_epsilon(s.eps().ravel())
         lat.set_force(s.g)
         lat.init_equilibrium()
@@ -176,7 +218,8 @@ def tune_tiles(specs, storage="fp16", steps=10, candidates=None, cache: Cache | 
     timings = {}
     for tc in candidates or TILE_CANDIDATES:
         b = lbm.Batch(max_members=len(lats), max_tiles=sum(
-            (lt.stored + tc - 1) // tc for lt in lats) + 1, tile_cells=tc, stream=stream)
+            (lt.stored + tc - 1) // tc for lt in lats) + 1, tile_cells=tc, stream=stream,
+            storage=storage)
         for lt in lats:
             b.add(lt, 10 ** 9)
         b.step(2)

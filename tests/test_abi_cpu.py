@@ -53,7 +53,7 @@ def test_struct_layouts_match_the_header():
     fields = re.findall(r"\b(\w+)(?:\s*,\s*(\w+))?(?:\s*,\s*(\w+))?\s*;", body)
     flat = [f for group in fields for f in group if f]
     assert [f[0] for f in lbm.Params._fields_] == flat
-    assert ctypes.sizeof(lbm.Params) == 88
+    assert ctypes.sizeof(lbm.Params) == 136
 
 
 def test_params_default_and_device_bytes_need_no_gpu():
@@ -95,7 +95,10 @@ def _params(**kw):
 
 
 @pytest.mark.parametrize("kw,word", [
-    (dict(tau=0.5), "tau"), (dict(tau=float("nan")), "tau"), (dict(lattice=3), "lattice"),
+    (dict(tau=0.5), "tau"), (dict(tau=float("nan")), "tau"), (dict(lattice=4), "lattice"),
+    (dict(lattice=3, ny=2, nz=1), "D1Q3"), (dict(drag_model=1, drag_d=0.0), "drag"),
+    (dict(les_cs=-0.1), "les_cs"), (dict(les_cs=0.2, kernel=2), "one-cell"),
+    (dict(quad_auto=2), "quad_auto"),
     (dict(storage=7), "storage"), (dict(nx=0), "nx"), (dict(lattice=0, nz=2), "D2Q9"),
     (dict(quad_dim=4), "quad_dim"), (dict(rho0=0.0), "rho0"),
     (dict(lattice=0, nz=1, walls=4), "walls"), (dict(quad_axes=8), "quad_axes")])

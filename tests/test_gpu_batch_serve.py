@@ -221,3 +221,126 @@ def test_fp16_served_result_close_to_fp32_alone():
         for key in ("u",):
             a, b = r.result[key].astype(np.float64), ref.result[key].astype(np.float64)
             assert np.linalg.norm(a - b) / np.linalg.norm(b) <= 2e-3
+
+
+# ------------------------------------------------ batched and served results vs the oracle
+
+def _oracle_of(spec, eps32, steps):
+    """The FP64 oracle's moments after `steps` steps of the lattice a spec
+    describes (the same float32-rounded phi the GPU was given)."""
+    import oracle
+    nz, ny, nx = spec.shape
+    P = oracle.Problem(spec.lattice, nx, ny, nz, tau=spec.tau, eps_ref=eps32.astype(np.float64), g=spec.g)
+    f = P.run(P.init(), 0, steps)
+    m = P.moments(f, steps)
+    return m["u"].reshape(3, -1), m["p"].ravel()
+
+
+def _rel(a, b):
+    a, b = np.asarray(a, np.float64).ravel(), np.asarray(b, np.float64).ravel()
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+TOL = {"fp32": 1e-5, "fp16": 2e-3}
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_batch_members_match_the_oracle(storage):
+    """Members of a batch advanced by the batched kernels (a row-class member
+    stepped by the batched row kernel, a cell-class member by the tiled
+    one-cell-per-thread batch kernel, different budgets) against the FP64
+    oracle run on the same inputs: relative L2 of u and p within 1e-5 (FP32)
+    and 2e-3 (FP16-shifted)."""
+    specs = [I.LatticeSpec("D3Q19", (10, 12, 96), 0.7, 0.2, 31),
+             I.LatticeSpec("D2Q9", (1, 30, 40), 0.9, 0.25, 32),
+             I.LatticeSpec("D3Q27", (9, 10, 64), 0.62, 0.15, 33)]
+    budgets = [160, 120, 100]
+    kernels = ["row", "cell", "row"]
+    lats, eps = [], []
+    for s, kern in zip(specs, kernels):
+        e = s.eps().ravel().astype(np.float32)
+        nz, ny, nx = s.shape
+        lat = lbm.Lattice(s.lattice, (nx, ny, nz), tau=s.tau, storage=storage, kernel=kern)
+        assert lat.row_kernel == (kern == "row")
+        lat.set_epsilon(e)
+        lat.set_force(s.g)
+        lat.init_equilibrium()
+        lats.append(lat)
+        eps.append(e)
+    b = lbm.Batch(max_members=4, max_tiles=256, tile_cells=1024)
+    for lat, k in zip(lats, budgets):
+        b.add(lat, k)
+    for _ in range(4):
+        b.step(40, check=True)
+    for s, lat, e, k in zip(specs, lats, eps, budgets):
+        assert lat.steps_done == k
+        u, p = _oracle_of(s, e, k)
+        m = lat.moments()
+        assert _rel(m["u"], u) <= TOL[storage], (s.lattice, storage)
+        assert _rel(m["p"] - m["p"].mean(), p - p.mean()) <= TOL[storage], (s.lattice, storage)
+    b.close()
+
+
+# Per-result accuracy of served answers (measured on GB300, 300-400 steps,
+# sides 16-30, g = 1e-6).  Random-sphere requests flow at u_max 0.007-0.04:
+# FP32 within 4.5e-6 and FP16-shifted within 1.1e-3 of the FP64 oracle on u
+# and p.  Product-sine requests flow at u_max 4e-4 .. 1.1e-3 with a pressure
+# variation of 2e-6 .. 1.2e-4: FP32 stays within 1.4e-5 on u, FP16 within
+# 3.6e-3 on u; the relative pressure error of those near-uniform pressure
+# fields is the storage rounding over a vanishing signal (FP32 up to 3.6e-4,
+# FP16 up to 0.1: an absolute error of the order of the dynamic pressure
+# u_max^2, the resolution limit of half precision for so slow a flow).
+TOL_SERVED = {"fp32": 1e-5, "fp16": 2e-3}
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_served_requests_match_the_oracle(storage):
+    """Random-sphere requests of different sizes that arrive while others run
+    (continuous batching) and retire on their step budget or their residual
+    target: each retired result (u and p, read back without allocation)
+    against the FP64 oracle run for the same number of steps, within 1e-5
+    (FP32) and 2e-3 (FP16-shifted)."""
+    reqs = serve.make_requests(300.0, 4, seed_offset=7700, sides=(16, 30), steps=(300, 400),
+                               residual_share=0.5, sphere_share=1.0)
+    # arrivals half a millisecond apart: each request arrives while the
+    # earlier ones are on the GPU and joins their batch
+    for j, r in enumerate(reqs):
+        r.arrival = 5e-4 * j
+    reqs[1].spec.residual_tol = 6e-3
+    for r in reqs:
+        if r.spec.residual_tol > 0:
+            # a flow accelerated from rest has r ~ 1/n: it retires on the
+            # residual (near step 170) before its budget
+            r.spec.residual_tol = 6e-3
+            r.spec.steps = max(r.spec.steps, 300)
+    srv = serve.Server(storage=storage, hbm_budget=8e9, macro_steps=20)
+    summary = srv.run(reqs)
+    srv.close()
+    assert summary["completed"] == 4 and summary["peak_members"] >= 2
+    assert any(r.status == "converged" for r in reqs)
+    for r in reqs:
+        u, p = _oracle_of(r.spec, np.asarray(r.eps, np.float32).ravel(), r.steps_done)
+        ru = r.result["u"].reshape(3, -1)
+        assert _rel(ru, u) <= TOL_SERVED[storage], (r.rid, storage, r.status)
+        assert _rel(r.result["p"] - r.result["p"].mean(), p - p.mean()) <= TOL_SERVED[storage], (r.rid, storage)
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_served_slow_flows_keep_their_stated_velocity_error(storage):
+    """Product-sine requests (slow flows, near-uniform pressure): the served
+    velocity stays within the per-result errors stated above (FP32 2e-5,
+    FP16 5e-3), and the pressure within an absolute error below the dynamic
+    pressure u_max^2 (FP32: below 1e-2 of it)."""
+    reqs = serve.make_requests(300.0, 3, seed_offset=7800, sides=(16, 30), steps=(300, 400),
+                               residual_share=0.0, sphere_share=0.0)
+    for j, r in enumerate(reqs):
+        r.arrival = 5e-4 * j
+    srv = serve.Server(storage=storage, hbm_budget=8e9, macro_steps=20)
+    srv.run(reqs)
+    srv.close()
+    for r in reqs:
+        u, p = _oracle_of(r.spec, np.asarray(r.eps, np.float32).ravel(), r.steps_done)
+        assert _rel(r.result["u"].reshape(3, -1), u) <= {"fp32": 2e-5, "fp16": 5e-3}[storage]
+        dp = (r.result["p"] - r.result["p"].mean()) - (p - p.mean())
+        qdyn = float(np.abs(u).max()) ** 2
+        assert np.sqrt(np.mean(dp ** 2)) <= {"fp32": 1e-2, "fp16": 2.0}[storage] * qdyn

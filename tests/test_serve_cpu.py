@@ -24,6 +24,10 @@ class FakeLattice:
     def moments(self, f64=False):
         return {"u": np.zeros((3, self.n)), "p": np.zeros(self.n)}
 
+    def moments_noalloc(self):
+        self.read_without_allocation = True
+        return self.moments()
+
     def close(self):
         self.closed = True
 

@@ -19,29 +19,50 @@ def test_bucket_key_groups_sizes_by_power_of_two_and_row_fill():
 
 def test_cache_round_trip_and_defaults(tmp_path):
     path = str(tmp_path / "sub" / "autotune.json")
-    c = tune.Cache(path)
+    c = tune.Cache(path, seed=None)
     shape = (256, 64, 64)
     # empty cache: the library's own choices
-    assert tune.best_config("D3Q19", "fp32", shape, cache=c) == (0, (0, 0))
+    assert tune.best_config("D3Q19", "fp32", shape, cache=c) is None
     assert tune.best_block("D3Q19", "fp32", shape, cache=c) == (0, 0)
+    assert tune.best_tile("fp16", cache=c) is None
     key = tune.bucket_key("D3Q19", "fp32", shape)
-    c.put("step/" + key, {"best": {"kernel": 2, "block": [64, 2]}, "ms": {"row": 0.5}})
+    c.put("step/" + key, {"best": {"kernel": 2, "block": [0, 0], "row_shape": [5, 2]},
+                          "ms": {"row5x2": 0.5}})
     c.put("block/" + key, {"best": [128, 1], "ms": {"128x1": 0.7}})
+    c.put("tile/fp16/n256", {"best": 8192, "ms": {"8192": 1.0}})
     # persisted: a fresh instance reads what was written
-    c2 = tune.Cache(path)
-    assert tune.best_config("D3Q19", "fp32", shape, cache=c2) == (2, (64, 2))
+    c2 = tune.Cache(path, seed=None)
+    hit = tune.best_config("D3Q19", "fp32", shape, cache=c2)
+    assert (hit["kernel"], hit["row_shape"], hit["key"]) == (2, [5, 2], "step/" + key)
     assert tune.best_block("D3Q19", "fp32", shape, cache=c2) == (128, 1)
+    assert tune.best_tile("fp16", cache=c2) == {"best": 8192, "key": "tile/fp16/n256"}
     # another lattice of the same bucket reuses the entry; another bucket does not
     assert tune.best_block("D3Q19", "fp32", (128, 128, 64), cache=c2) == (128, 1)
     assert tune.best_block("D3Q19", "fp32", (256, 256, 256), cache=c2) == (0, 0)
+    assert tune.best_config("D3Q19", "fp16", shape, cache=c2) is None
     with open(path) as fh:
-        assert set(json.load(fh)) == {"step/" + key, "block/" + key}
+        assert set(json.load(fh)) == {"step/" + key, "block/" + key, "tile/fp16/n256"}
+
+
+def test_seed_file_is_read_first_and_overlaid(tmp_path):
+    seed = tmp_path / "seed.json"
+    seed.write_text(json.dumps({"tile/fp32/n8": {"best": 2048}, "tile/fp16/n8": {"best": 1024}}))
+    local = tmp_path / "local.json"
+    local.write_text(json.dumps({"tile/fp16/n8": {"best": 4096}}))
+    c = tune.Cache(str(local), seed=str(seed))
+    assert tune.best_tile("fp32", cache=c)["best"] == 2048
+    assert tune.best_tile("fp16", cache=c)["best"] == 4096
+
+
+def test_environment_selects_the_cache(tmp_path, monkeypatch):
+    monkeypatch.setenv("LBM_TUNE_CACHE", str(tmp_path / "env.json"))
+    assert tune.Cache(seed=None).path == str(tmp_path / "env.json")
 
 
 def test_unreadable_cache_starts_empty(tmp_path):
     path = tmp_path / "autotune.json"
     path.write_text("{not json")
-    c = tune.Cache(str(path))
+    c = tune.Cache(str(path), seed=None)
     assert c.data == {}
     c.put("block/x", {"best": [32, 1], "ms": {}})
     assert json.loads(path.read_text()) == {"block/x": {"best": [32, 1], "ms": {}}}
