@@ -59,7 +59,7 @@ namespace {
 
 constexpr int kTypes = 8;  // (lattice 0..3) x (storage fp32, fp16); D1Q3 members use the tiled kernel only
 constexpr int kBatchBlock = 256;
-constexpr int kPitchClasses = 8;                     // row pitch 64/128/256/512, with or without y/z walls
+constexpr int kPitchClasses = 8;                     // shape codes: row pitch 256/512 (2, 3), with or without y/z walls (+4)
 constexpr int kRowClasses = kTypes * kPitchClasses;  // batched row kernel classes
 constexpr int kParts = 2 * kRowClasses;  // class x parity of the member's time at the replay start
 constexpr int kLanes = kTypes + kParts;  // concurrent chains of a replay
@@ -212,7 +212,7 @@ struct HostMember {
   int row_class;  // batched row kernel class, or -1 (one-cell-per-thread tiles)
   LatticeDev pushed;  // the descriptor as the device holds it (valid after the first push)
   int group;      // parity of the member's time when the row tables were built
-  int nrows;      // fluid rows (row members)
+  int nrows;      // work items of the batched row kernel (tiles of up to 8 fluid rows)
   long long last_check_n;
   bool have_prev;
   double stats[kRedWidth];
@@ -366,7 +366,8 @@ extern "C" int lbm_vanse_batch_add(lbm_vanse_batch_t b, lbm_vanse_t h, long long
       !(p.les_cs > 0.0) && m.lattice != LBM_D1Q3 && m.nx >= 8 && m.nxp <= 512 && !(m.walls & 1u) &&
       m.ncell <= 0x7fffffffLL) {
     const int nyf = (m.walls & 2u) ? m.ny - 2 : m.ny, nzf = (m.walls & 4u) ? m.nz - 2 : m.nz;
-    const int pclass = (m.nxp <= 64 ? 0 : (m.nxp <= 128 ? 1 : (m.nxp <= 256 ? 2 : 3))) | ((m.walls & 6u) ? 4 : 0);
+    const int pitch = m.nxp <= 256 ? 256 : 512;
+    const int pclass = (pitch == 256 ? 2 : 3) | ((m.walls & 6u) ? 4 : 0);
     const int cls = hm.type * kPitchClasses + pclass;
     if (b->class_grid[cls] == 0) {
       const int g = row_class_grid(cls);
@@ -374,7 +375,9 @@ extern "C" int lbm_vanse_batch_add(lbm_vanse_batch_t b, lbm_vanse_t h, long long
     }
     if (nyf >= 1 && nzf >= 1 && b->class_grid[cls] > 0) {
       hm.row_class = cls;
-      hm.nrows = nyf * nzf;
+      // tiles of R rows of one plane (the kernel's tile_rows)
+      const int R = std::max(1, std::min(8, pitch / (int)m.nxp));
+      hm.nrows = (nyf + R - 1) / R * nzf;
     }
   }
   if (hm.row_class < 0) {
@@ -454,7 +457,7 @@ static int upload_tables(lbm_vanse_batch_t b) {
   cudaStream_t s = b->stream;
   cudaError_t e = cudaSuccess;
   if (b->dirty) {
-    // class row tables: the rows of each class, member after member
+    // class item tables: the tiles of each class, member after member
     b->rows_host.clear();
     b->row_begin_host.assign(nm, 0);
     b->cls_host.assign(kParts, make_int2(0, 0));

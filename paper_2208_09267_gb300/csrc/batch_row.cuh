@@ -1,29 +1,29 @@
-// batch_row.cuh -- the row-staged fused step (step_row.cuh) over the rows of
-// many lattices in one persistent launch.
+// batch_row.cuh -- the row-staged fused step (step_row.cuh) over the tiles
+// of many lattices in one persistent launch.
 //
 // A batch class is one (lattice, storage, row pitch, walls or none)
-// combination.  Its rows are the fluid rows of every member of the class,
-// member after member; the class row table maps a row to its member.  The
-// rows are dealt to the blocks in runs of up to 8 consecutive rows (block b
-// takes runs b, b + G, b + 2G, ..., G = grid size; shorter runs when the
-// class has few rows, so that every block gets work), so that a block's next
-// row is usually the next row of the same member.  Each row carries its own
-// member: the producer warp looks the member up when the row leaves the
-// current member's row range, copies the member's device descriptor into
-// the stage beside the row's populations and fields, and records in the
-// stage context whether the row is skipped (member's step budget spent) or
-// a check step.  Members keep their own time: the rows of a class are split
-// by the parity of the member's time at the start of a replay, and each
-// part is stepped by the even or odd instantiation as the steps alternate.
-// The consumers update the row with the same per-cell code as a lattice
-// stepped alone (update_row_chunk), so a member's populations are
-// bit-identical alone and in any batch.
+// combination.  Its work items are the tiles (R consecutive fluid rows of
+// one plane, R = min(8, PITCH / nxp): short rows are staged several at a
+// time) of every member of the class, member after member; the class item
+// table maps an item to its member.  The items are dealt to the blocks in
+// runs of up to 8 consecutive items (block b takes runs b, b + G, b + 2G,
+// ..., G = grid size; shorter runs when the class has few items, so that
+// every block gets work), so that a block's next tile is usually the next
+// tile of the same member.  Each item carries its own member: the producer
+// warp looks the member up when the item leaves the current member's range,
+// copies the member's device descriptor into the stage beside the tile's
+// populations and fields, and records in the stage context whether the
+// tile is skipped (member's step budget spent) or a check step.  Members keep
+// their own time: the items of a class are split by the parity of the
+// member's time at the start of a replay, and each part is stepped by the
+// even or odd instantiation as the steps alternate.  The consumers update
+// the tile with the same per-cell code as a lattice stepped alone
+// (update_row_chunk), so a member's populations are bit-identical alone and
+// in any batch.
 //
-// Stage depth follows the row pitch: short rows give small stages, so more
-// rows are in flight per block (up to 12).  Check-step sums are reduced per
-// warp and added into per-member FP64 sums with atomics when the row's
-// member changes (their summation order, not the per-cell values, depends
-// on the schedule).
+// Check-step sums are reduced per warp and added into per-member FP64 sums
+// with atomics when the item's member changes (their summation order, not
+// the per-cell values, depends on the schedule).
 #pragma once
 
 #include "step_row.cuh"
@@ -35,15 +35,16 @@ constexpr int kDescBytes = (int)sizeof(LatticeDev);
 
 // Stage context of the batched kernel.
 struct BatchRowCtx {
-  RowCtx rc;
+  RowCtx rc[kMaxTileRows];
+  int nr;      // rows of the tile
   int member;  // slot in the member table
   int flags;   // bit 0: skip, bit 2: check step
   float dn, dn_force;  // steps since the member's phi and force references
 };
 
-// Row sequence of a block: runs blockIdx.x, blockIdx.x + G, ... of len
-// rows each (len = nrows / (8 G), clamped to 1..8), cut at nrows.  Producer
-// and consumers walk it identically.
+// Item sequence of a block: runs blockIdx.x, blockIdx.x + G, ... of len
+// items each (len = nitems / (8 G), clamped to 1..8), cut at nitems.
+// Producer and consumers walk it identically.
 struct RowRuns {
   int run, t, nrows, len;
   __device__ __forceinline__ explicit RowRuns(int n) : run(blockIdx.x), t(0), nrows(n) {
@@ -90,15 +91,15 @@ __device__ __forceinline__ void flush_member_sums(RedAcc &acc, double *sums) {
   }
 }
 
-// REDC: a launch of a check replay (rows may carry the check flag).  RS 2:
+// REDC: a launch of a check replay (tiles may carry the check flag).  RS 2:
 // the first step of a replay, where a member's phi refresh since its last
 // step is still pending (its descriptor tells); RS 0: later steps (the
 // descriptors' shifts are committed only after the replay, so they must not
 // be read as pending there).
 template <class LAT, class ST, int P, bool WALLS, bool ODD, bool REDC, int RS, int NSTAGE, int MINB>
 __global__ void __launch_bounds__(row_threads<MINB>(), MINB)
-    batch_row_kernel(const BatchMember *__restrict__ members, const int *__restrict__ row_member,
-                     const int *__restrict__ row_begin, const int2 *__restrict__ cls,
+    batch_row_kernel(const BatchMember *__restrict__ members, const int *__restrict__ item_member,
+                     const int *__restrict__ item_begin, const int2 *__restrict__ cls,
                      double *__restrict__ member_sums, int *status, int k, int kmax, int check) {
   constexpr int kStage = BatchRowCfg<LAT, ST, P>::kStage;
   constexpr int kConsumerWarps = row_consumers<MINB>();
@@ -121,22 +122,20 @@ __global__ void __launch_bounds__(row_threads<MINB>(), MINB)
     mbar_fence_init();
   }
   __syncthreads();
-  // the class's rows are row_member[base, base + nrows)
-  const int base = cls->x, nrows = cls->y;
+  // the class's items are item_member[base, base + nitems)
+  const int base = cls->x, nitems = cls->y;
   const unsigned limit = kWaitSpins;
 
   if (warp == kConsumerWarps) {
     // ---------------- producer warp
     int cur = -1;  // member whose copies c0, c1 are set up
-    RowCopy c0, c1;
+    TileCopy c0, c1;
     float dn_m = 0.f, dnf_m = 0.f;
-    unsigned row_bytes = 0;
-    int ny = 1, nz = 1, nxp = 8, y0 = 0, z0 = 0, nyf = 1, rb = 0, re = 0, flags_m = 0;
-    int prev_r = -2, y = 0, z = 0;
+    int ny = 1, nz = 1, nxp = 8, y_first = 0, z_first = 0, nyf = 1, R = 1, tpp = 1, rb = 0, re = 0, flags_m = 0;
     unsigned walls = 0;
     const LatticeDev *Lg = nullptr;
     int issued_upto = -1;
-    RowRuns runs(nrows);
+    RowRuns runs(nitems);
     int j = 0;
     for (int r = runs.row(); r >= 0; runs.next(), r = runs.row(), ++j) {
       const int s = j % NSTAGE;
@@ -149,51 +148,42 @@ __global__ void __launch_bounds__(row_threads<MINB>(), MINB)
           break;
         }
       }
-      // the row's member: the current one while r stays in its row range
-      const int m = (r >= rb && r < re) ? cur : row_member[base + r];
+      // the item's member: the current one while r stays in its item range
+      const int m = (r >= rb && r < re) ? cur : item_member[base + r];
       if (m != cur) {
         cur = m;
         const BatchMember &M = members[m];
         Lg = M.L;
         const long long budget = M.budget;
         const long long last = (budget < kmax ? budget : kmax) - 1;
-        rb = row_begin[m];
+        rb = item_begin[m];
         ny = Lg->ny;
         nz = Lg->nz;
         nxp = Lg->nxp;
         walls = Lg->walls;
-        y0 = (walls & 2u) ? 1 : 0;
-        z0 = (walls & 4u) ? 1 : 0;
+        y_first = (walls & 2u) ? 1 : 0;
+        z_first = (walls & 4u) ? 1 : 0;
         nyf = (walls & 2u) ? ny - 2 : ny;
-        re = rb + nyf * ((walls & 4u) ? nz - 2 : nz);
-        prev_r = -2;
-        c0 = make_row_copy<LAT, ST, ODD, P>(*Lg, lane);
-        c1 = make_row_copy<LAT, ST, ODD, P>(*Lg, lane + 32);
-        row_bytes = (unsigned)__reduce_add_sync(0xffffffffu, c0.bytes + c1.bytes) + (unsigned)kDescBytes;
+        R = tile_rows(P, nxp);
+        tpp = (nyf + R - 1) / R;
+        re = rb + tpp * ((walls & 4u) ? nz - 2 : nz);
+        c0 = make_tile_copy<LAT, ST, ODD, P>(*Lg, lane);
+        c1 = make_tile_copy<LAT, ST, ODD, P>(*Lg, lane + 32);
         flags_m = (k >= budget ? 1 : 0) | (REDC && check && k == last ? 4 : 0);
         // converted once per member, not per cell
         const long long n = Lg->n + k;
         dn_m = (float)(n - Lg->n_eps);
         dnf_m = (float)(n - Lg->n_force);
       }
-      if (r == prev_r + 1) {
-        // the next row of the same member
-        if (++y == y0 + nyf) {
-          y = y0;
-          ++z;
-        }
-      } else {
-        const int lr = r - rb;
-        y = y0 + lr % nyf;
-        z = z0 + lr / nyf;
-      }
-      prev_r = r;
-      const int cdy = lane % 3 - 1, cdz = lane / 3 - 1;
-      const bool sol = lane < 9 && wall_row(walls, y + cdy, z + cdz, ny, nz);
-      const unsigned solid = __ballot_sync(0xffffffffu, sol) & 0x1ffu;
-      if (lane < 9) ctx[s].rc.base[cdz + 1][cdy + 1] = (wrapi(z + cdz, nz) * ny + wrapi(y + cdy, ny)) * nxp;
+      const int lt = r - rb;
+      const int tz = lt / tpp, ty = lt - tz * tpp;
+      const int y0 = y_first + ty * R, z = z_first + tz, nr = min(R, nyf - ty * R);
+      fill_row_ctx(ctx[s].rc, y0, z, nr, ny, nz, nxp, walls, lane);
+      const unsigned bytes =
+          __reduce_add_sync(0xffffffffu, tile_copy_bytes(c0, nr, nxp) + tile_copy_bytes(c1, nr, nxp)) +
+          (unsigned)kDescBytes;
       if (lane == 0) {
-        ctx[s].rc.solid = solid;
+        ctx[s].nr = nr;
         ctx[s].member = m;
         ctx[s].flags = flags_m;
         ctx[s].dn = dn_m;
@@ -205,12 +195,12 @@ __global__ void __launch_bounds__(row_threads<MINB>(), MINB)
         if (lane == 0) mbar_arrive(&full[s]);  // nothing to stage: the phase completes
       } else {
         if (lane == 0) {
-          mbar_arrive_expect_tx(&full[s], row_bytes);
+          mbar_arrive_expect_tx(&full[s], bytes);
           bulk_g2s(&descs[s], Lg, (unsigned)kDescBytes, &full[s]);
         }
         __syncwarp();
-        issue_copy(c0, stage, &full[s], y, z, ny, nz, nxp, walls);
-        issue_copy(c1, stage, &full[s], y, z, ny, nz, nxp, walls);
+        issue_tile_copy(c0, stage, &full[s], y0, z, nr, ny, nz, nxp, walls, nxp);
+        issue_tile_copy(c1, stage, &full[s], y0, z, nr, ny, nz, nxp, walls, nxp);
       }
       issued_upto = j;
       __syncwarp();
@@ -224,9 +214,9 @@ __global__ void __launch_bounds__(row_threads<MINB>(), MINB)
     RedAcc acc;
 #pragma unroll
     for (int q = 0; q < kRedWidth; ++q) acc.v[q] = 0.0;
-    int red_m = -1;       // member whose check sums acc holds
-    int chunk = 0;  // chunks dealt so far, modulo the consumer warps (all warps agree)
-    RowRuns runs(nrows);
+    int red_m = -1;  // member whose check sums acc holds
+    int rot = 0;     // chunks dealt so far, modulo the consumer warps (all warps agree)
+    RowRuns runs(nitems);
     int j = 0;
     for (int r = runs.row(); r >= 0; runs.next(), r = runs.row(), ++j) {
       const int s = j % NSTAGE;
@@ -249,14 +239,17 @@ __global__ void __launch_bounds__(row_threads<MINB>(), MINB)
         }
         const long long n = Lm.n + k;
         const float dn = ctx[s].dn, dn_force = ctx[s].dn_force;
-        const int nchunks = (Lm.nx + 31) >> 5;
-        const int first = (warp - chunk + kConsumerWarps) % kConsumerWarps;
-        for (int c = first; c < nchunks; c += kConsumerWarps) {
-          const int x = (c << 5) + lane;
-          if (red) update_row_chunk<LAT, ST, ODD, REDC, WALLS, P, RS>(Lm, data, ctx[s].rc, n, dn, dn_force, x, acc);
-          else update_row_chunk<LAT, ST, ODD, false, WALLS, P, RS>(Lm, data, ctx[s].rc, n, dn, dn_force, x, acc);
+        const int ncr = (Lm.nx + 31) >> 5;
+        const int nch = ctx[s].nr * ncr;
+        const int first = (warp - rot + kConsumerWarps) % kConsumerWarps;
+        for (int c = first; c < nch; c += kConsumerWarps) {
+          const int t = c / ncr, x = ((c - t * ncr) << 5) + lane;
+          if (red)
+            update_row_chunk<LAT, ST, ODD, REDC, WALLS, P, RS>(Lm, data, t, ctx[s].rc[t], n, dn, dn_force, x, acc);
+          else
+            update_row_chunk<LAT, ST, ODD, false, WALLS, P, RS>(Lm, data, t, ctx[s].rc[t], n, dn, dn_force, x, acc);
         }
-        chunk = (chunk + nchunks) % kConsumerWarps;
+        rot = (rot + nch) % kConsumerWarps;
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[s]);
@@ -267,42 +260,42 @@ __global__ void __launch_bounds__(row_threads<MINB>(), MINB)
 
 // Host side: launch of one class part.
 template <class LAT, class ST, int P, bool WALLS, bool ODD, bool REDC, int RS>
-cudaError_t launch_batch_row_t(const BatchMember *members, const int *row_member, const int *row_begin,
+cudaError_t launch_batch_row_t(const BatchMember *members, const int *item_member, const int *item_begin,
                                const int2 *cls, double *member_sums, int *status, int k, int kmax,
                                int check, int grid, cudaStream_t s) {
   using C = BatchRowCfg<LAT, ST, P>;
   const int smem = C::kStage * C::kStages;
   batch_row_kernel<LAT, ST, P, WALLS, ODD, REDC, RS, C::kStages, C::kMinB><<<grid, row_threads<C::kMinB>(), smem, s>>>(
-      members, row_member, row_begin, cls, member_sums, status, k, kmax, check);
+      members, item_member, item_begin, cls, member_sums, status, k, kmax, check);
   return cudaGetLastError();
 }
 
 template <class LAT, class ST, int P, bool WALLS, bool ODD, bool REDC>
-cudaError_t launch_batch_row_rs(bool first, const BatchMember *members, const int *row_member,
-                                const int *row_begin, const int2 *cls, double *member_sums, int *status, int k,
+cudaError_t launch_batch_row_rs(bool first, const BatchMember *members, const int *item_member,
+                                const int *item_begin, const int2 *cls, double *member_sums, int *status, int k,
                                 int kmax, int check, int grid, cudaStream_t s) {
   if (first)
-    return launch_batch_row_t<LAT, ST, P, WALLS, ODD, REDC, 2>(members, row_member, row_begin, cls, member_sums,
+    return launch_batch_row_t<LAT, ST, P, WALLS, ODD, REDC, 2>(members, item_member, item_begin, cls, member_sums,
                                                                status, k, kmax, check, grid, s);
-  return launch_batch_row_t<LAT, ST, P, WALLS, ODD, REDC, 0>(members, row_member, row_begin, cls, member_sums,
+  return launch_batch_row_t<LAT, ST, P, WALLS, ODD, REDC, 0>(members, item_member, item_begin, cls, member_sums,
                                                              status, k, kmax, check, grid, s);
 }
 
 // first: the first step of the replay (k == 0)
 template <class LAT, class ST, int P, bool WALLS>
 cudaError_t launch_batch_row_t(bool odd, bool redc, bool first, const BatchMember *members,
-                               const int *row_member, const int *row_begin, const int2 *cls,
+                               const int *item_member, const int *item_begin, const int2 *cls,
                                double *member_sums, int *status, int k, int kmax, int check, int grid,
                                cudaStream_t s) {
   if (odd) {
-    if (redc) return launch_batch_row_rs<LAT, ST, P, WALLS, true, true>(first, members, row_member, row_begin, cls,
+    if (redc) return launch_batch_row_rs<LAT, ST, P, WALLS, true, true>(first, members, item_member, item_begin, cls,
                                                                          member_sums, status, k, kmax, check, grid, s);
-    return launch_batch_row_rs<LAT, ST, P, WALLS, true, false>(first, members, row_member, row_begin, cls,
+    return launch_batch_row_rs<LAT, ST, P, WALLS, true, false>(first, members, item_member, item_begin, cls,
                                                                 member_sums, status, k, kmax, check, grid, s);
   }
-  if (redc) return launch_batch_row_rs<LAT, ST, P, WALLS, false, true>(first, members, row_member, row_begin, cls,
+  if (redc) return launch_batch_row_rs<LAT, ST, P, WALLS, false, true>(first, members, item_member, item_begin, cls,
                                                                         member_sums, status, k, kmax, check, grid, s);
-  return launch_batch_row_rs<LAT, ST, P, WALLS, false, false>(first, members, row_member, row_begin, cls,
+  return launch_batch_row_rs<LAT, ST, P, WALLS, false, false>(first, members, item_member, item_begin, cls,
                                                                member_sums, status, k, kmax, check, grid, s);
 }
 

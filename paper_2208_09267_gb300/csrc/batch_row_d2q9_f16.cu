@@ -4,23 +4,19 @@
 
 namespace lbm {
 
-// shape class: bits 0-1 row pitch 64, 128, 256, 512; bit 2 walls on y/z;
+// shape class: bits 0-1 row pitch (2: 256, 3: 512); bit 2 walls on y/z;
 // odd: the step parity of the launched part; redc: a check replay; first:
 // the replay's first step
 cudaError_t launch_batch_row_d2q9_f16(int shape, int odd, int redc, int first, const BatchMember *members,
-                                     const int *row_member, const int *row_begin, const int2 *cls,
+                                     const int *item_member, const int *item_begin, const int2 *cls,
                                      double *member_sums, int *status, int k, int kmax, int check, int grid,
                                      cudaStream_t s) {
 #define LBM_BR(P, W)                                                                                       \
-  return launch_batch_row_t<D2Q9, __half, P, W>(odd != 0, redc != 0, first != 0, members, row_member, row_begin, \
+  return launch_batch_row_t<D2Q9, __half, P, W>(odd != 0, redc != 0, first != 0, members, item_member, item_begin, \
                                              cls, member_sums, status, k, kmax, check, grid, s)
   switch (shape) {
-    case 0: LBM_BR(64, false);
-    case 1: LBM_BR(128, false);
     case 2: LBM_BR(256, false);
     case 3: LBM_BR(512, false);
-    case 4: LBM_BR(64, true);
-    case 5: LBM_BR(128, true);
     case 6: LBM_BR(256, true);
     case 7: LBM_BR(512, true);
   }
@@ -30,12 +26,8 @@ cudaError_t launch_batch_row_d2q9_f16(int shape, int odd, int redc, int first, c
 
 int configure_batch_row_d2q9_f16(int shape) {
   switch (shape) {
-    case 0: return configure_batch_row_t<D2Q9, __half, 64, false>();
-    case 1: return configure_batch_row_t<D2Q9, __half, 128, false>();
     case 2: return configure_batch_row_t<D2Q9, __half, 256, false>();
     case 3: return configure_batch_row_t<D2Q9, __half, 512, false>();
-    case 4: return configure_batch_row_t<D2Q9, __half, 64, true>();
-    case 5: return configure_batch_row_t<D2Q9, __half, 128, true>();
     case 6: return configure_batch_row_t<D2Q9, __half, 256, true>();
     case 7: return configure_batch_row_t<D2Q9, __half, 512, true>();
   }

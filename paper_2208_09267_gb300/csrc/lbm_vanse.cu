@@ -329,7 +329,7 @@ extern "C" int lbm_vanse_create(const lbm_vanse_params *p, lbm_vanse_t *out) {
       delete h;
       return fail(nullptr, LBM_EINVAL, "the row-staged kernel does not fit this lattice");
     }
-    if (ok && p->kernel == 0 && p->nx < 64) h->ls.row = 0;  // short rows: one cell per thread
+    if (ok && p->kernel == 0 && p->nx < 32) h->ls.row = 0;  // short rows: one cell per thread
     if (h->ls.row) h->nblocks = h->ls.row_grid;
   }
   const int nblocks_alloc = h->nblocks > (int)kRowGridBound ? h->nblocks : (int)kRowGridBound;

@@ -1,27 +1,34 @@
 // step_row.cuh -- persistent row kernel: the fused step of step_fast.cuh with
 // its inputs staged in shared memory by TMA bulk copies.
 //
-// Work item: one fluid x-row (y, z) of the lattice, all nx cells.  A block
-// keeps NSTAGE rows in flight: while the threads update row j, the bulk
-// copies of row j + NSTAGE - 1 are landing.  Per row and step the block
-// stages
-//   - the Q population rows it reads: at even n plane i of its own row; at
-//     odd n plane opp(i) of row (y - c_iy, z - c_iz) (the x shift of -c_ix
-//     is a modular index into the staged row), or plane i of its own row when
-//     that neighbour row is a wall layer (halfway bounce-back);
-//   - phi_ref on the rows (y + dy, z + dz), dy, dz in {-1, 0, 1} (odd steps;
-//     these also give the shift sigma of every neighbour) or the 5-point
-//     cross (even steps), and d_t phi on the 5-point cross when phi varies;
-// each as one contiguous cp.async.bulk of nx elements, completing on one
-// mbarrier per stage.  Updated populations are written straight to global
-// memory (coalesced, in place, AA pattern).
+// Work item: a tile of R consecutive fluid x-rows (y0 .. y0 + R - 1) of one
+// z-plane, all nx cells of each, R = min(8, PITCH / nxp) (1 for rows of more
+// than half the pitch).  A block keeps NSTAGE tiles in flight: while the
+// threads update tile j, the bulk copies of tile j + NSTAGE - 1 are landing.
+// Per tile and step the block stages, rows stored at their pitch nxp:
+//   - the Q population blocks it reads (R rows each): at even n plane i of
+//     its own rows; at odd n plane opp(i) of rows (y - c_iy, z - c_iz) (the x
+//     shift of -c_ix is a modular index into the staged row), or plane i of
+//     the own row where that neighbour row is a wall layer (halfway
+//     bounce-back);
+//   - the shift sigma (phi_ref rounded to half) of the rows y0 - 1 .. y0 + R
+//     of the planes z - 1, z, z + 1 (odd steps: every neighbour's shift) or
+//     of the own rows (even steps);
+//   - phi_ref on the rows y0 - 1 .. y0 + R of plane z and on the tile's rows
+//     of the planes z - 1 and z + 1 (the 5-point cross of every cell), and
+//     d_t phi on the same rows when phi varies;
+// each block as one cp.async.bulk of consecutive stored rows (more where the
+// rows wrap around periodically or a wall layer substitutes the own row),
+// completing on one mbarrier per stage.  Tiles of several short rows cut
+// the number of copies per cell: the producer warp's copy issue, not DRAM,
+// bounds rows of a few dozen cells staged one by one.
 //
 // Requirements (checked by the host before choosing this kernel): rows
 // stored at a pitch nxp that is a multiple of 8 elements (so every copy
-// starts and ends on a 16-byte boundary), nxp <= 512, fewer than 2^31 stored
-// cells, walls only on y and/or z.  Every wait is bounded: a block that waits too long
-// records the failure in L.status, drains its copies (again bounded) and
-// leaves; the host reports LBM_ETIMEOUT.
+// starts and ends on a 16-byte boundary), nxp <= PITCH <= 512, fewer than
+// 2^31 stored cells, walls only on y and/or z.  Every wait is bounded: a
+// block that waits too long records the failure in L.status, drains its
+// copies (again bounded) and leaves; the host reports LBM_ETIMEOUT.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -35,15 +42,33 @@ namespace lbm {
 #ifndef LBM_ROW_CONSUMERS
 #define LBM_ROW_CONSUMERS 7
 #endif
+#ifndef LBM_ROW_CONSUMERS_F16
+#define LBM_ROW_CONSUMERS_F16 6
+#endif
 // Consumer warps per block (+ one producer warp).  Two blocks per SM (MINB
 // 2) take 7: every SM sub-partition then holds four warps of up to 128
 // registers.  Where a stage is too large for two blocks per SM (MINB 1: rows
-// of 512 cells, D3Q27) one block takes 15, so the SM keeps 16 warps.
-template <int MINB>
-constexpr int row_consumers() { return MINB == 1 ? 15 : LBM_ROW_CONSUMERS; }
+// of 512 cells, D3Q27) one block takes 15, so the SM keeps 16 warps.  FP16
+// D2Q9/D3Q19 blocks also have a storer warp and update two cells per lane
+// (more live registers): 6 consumers (14 with MINB 1) keep them at 16 warps
+// per SM, 128 registers each.
+template <int MINB, bool PAIR = false>
+constexpr int row_consumers() {
+  return PAIR ? (MINB == 1 ? 14 : LBM_ROW_CONSUMERS_F16) : (MINB == 1 ? 15 : LBM_ROW_CONSUMERS);
+}
 template <int MINB>
 constexpr int row_threads() { return (row_consumers<MINB>() + 1) * 32; }
+// FP16 plain steps of D2Q9/D3Q19 update two adjacent cells per lane
+// (update_row_pair); D3Q27's larger state would spill
+template <class LAT, class ST>
+constexpr bool row_pair_lattice() { return sizeof(ST) == 2 && LAT::Q <= 19; }
 constexpr unsigned kWaitSpins = 1u << 22;  // bounded mbarrier wait
+constexpr int kMaxTileRows = 8;
+
+// rows per tile of a lattice with row pitch nxp in a kernel of stage pitch PITCH
+__host__ __device__ constexpr int tile_rows(int pitch, int nxp) {
+  return pitch / nxp < 1 ? 1 : (pitch / nxp > kMaxTileRows ? kMaxTileRows : pitch / nxp);
+}
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
@@ -91,55 +116,48 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsig
   return false;
 }
 
-// Shared-memory layout of one stage.  Rows are stored at a compile-time
-// pitch (PITCH elements >= nx) so that every shared-memory address below is
-// a register plus an immediate.  Order: Q population rows, the shift rows
-// (half; the 3x3 block of rows (y+dy, z+dz) at odd steps, the own row at even
-// steps), the phi_ref rows of the 5-point cross and the d_t phi rows of the
-// cross (2D: the 3 rows y-1, y, y+1).
+// Shared-memory layout of one stage, in slots of PITCH elements (a block of
+// rows at pitch nxp fills at most its slots).  Order: the Q population
+// blocks (R rows each); the shift blocks (half; odd steps: three slots per
+// plane z + dz, dz = -1, 0, 1 (2D: plane z only), holding rows y0 - 1 ..
+// y0 + R; even steps: one slot with the tile's own rows); phi_ref (plane z:
+// three slots, rows y0 - 1 .. y0 + R; 3D: then one slot each for planes z - 1
+// and z + 1, the tile's rows); d_t phi in the same layout.
 template <class LAT, class ST, bool ODD, int PITCH>
 struct RowLayout {
-  static constexpr int kSigRows = ODD ? (LAT::D == 2 ? 3 : 9) : 1;
-  static constexpr int kEpsRows = LAT::D == 2 ? 3 : 5;
-  static constexpr int kDepsRows = kEpsRows;
+  static constexpr int kSigSlots = ODD ? (LAT::D == 2 ? 3 : 9) : 1;
+  static constexpr int kEpsSlots = LAT::D == 2 ? 3 : 5;
   static constexpr int kPopBytes = PITCH * (int)sizeof(ST);
   static constexpr int kSigBytes = PITCH * 2;
   static constexpr int kRowBytes = PITCH * 4;
   static constexpr int kSigOff = LAT::Q * kPopBytes;
-  static constexpr int kEpsOff = kSigOff + kSigRows * kSigBytes;
-  static constexpr int kDepsOff = kEpsOff + kEpsRows * kRowBytes;
-  static constexpr int kStageBytes = kDepsOff + kDepsRows * kRowBytes;
+  static constexpr int kEpsOff = kSigOff + kSigSlots * kSigBytes;
+  static constexpr int kDepsOff = kEpsOff + kEpsSlots * kRowBytes;
+  static constexpr int kStageBytes = kDepsOff + kEpsSlots * kRowBytes;
 };
 
-// Row (dy, dz) of the 5-point cross: 0 centre, 1 y-1, 2 y+1, 3 z-1, 4 z+1
-// (2D: dy + 1).
+// shift block of plane z + dz at odd steps
 template <class LAT>
-__host__ __device__ constexpr int cross_index(int dy, int dz) {
-  return LAT::D == 2 ? dy + 1 : (dz == 0 ? (dy == 0 ? 0 : (dy < 0 ? 1 : 2)) : (dz < 0 ? 3 : 4));
-}
-
-// Shift row (dy, dz): 3x3 block at odd steps (2D: dy + 1), own row at even.
-template <class LAT, bool ODD>
-__host__ __device__ constexpr int sig_index(int dy, int dz) {
-  return ODD ? (LAT::D == 2 ? dy + 1 : (dz + 1) * 3 + (dy + 1)) : 0;
+__host__ __device__ constexpr int sig_block(int dz) {
+  return LAT::D == 2 ? 0 : dz + 1;
 }
 
 __device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
-// Per-row quantities shared by the block (computed once per row).
+// Per-row quantities (computed by the producer, once per row of a tile).
 struct RowCtx {
   int base[3][3];   // cell index of x = 0 on row (y+dy, z+dz), [dz+1][dy+1]
   unsigned solid;   // bit (dz+1)*3+(dy+1): that neighbour row is a wall layer
 };
 
-// Offsets (dy, dz) of the 5-point cross rows (2D: e - 1, 0).
-template <class LAT>
-__host__ __device__ constexpr int cross_dy(int e) {
-  return LAT::D == 2 ? e - 1 : (e == 1 ? -1 : (e == 2 ? 1 : 0));
-}
-template <class LAT>
-__host__ __device__ constexpr int cross_dz(int e) {
-  return LAT::D == 2 ? 0 : (e == 3 ? -1 : (e == 4 ? 1 : 0));
+// A staged tile: first row, plane, rows.
+struct TileCtx {
+  int y0, z, nr;
+};
+
+// Is row (y, z) a wall layer?
+__device__ __forceinline__ bool wall_row(unsigned walls, int y, int z, int ny, int nz) {
+  return ((walls & 2u) && (y <= 0 || y >= ny - 1)) || ((walls & 4u) && (z <= 0 || z >= nz - 1));
 }
 
 // (c_iy, c_iz) of direction i (runtime i), by unrolled selects: no table in
@@ -156,33 +174,33 @@ __device__ __forceinline__ void dir_yz(int i, int &cy, int &cz) {
   }
 }
 
-// One bulk copy of the producer warp, set up once per launch: lane l owns
-// copies l and l + 32 of every row.  Per row only the source row changes.
-struct RowCopy {
+// One block of a tile's bulk copies, owned by one producer lane and set up
+// once per launch (or per batch member): block row k (0 <= k < nr + extra)
+// is source row (y0 + k + dy0, z + dz), wrapped periodically; a population
+// block read from a neighbour row takes the own row (y0 + k, z) of plane
+// src_own where that neighbour row is a wall layer.
+struct TileCopy {
   const char *src;      // field (population plane included) at row base 0
-  const char *src_own;  // population copies: the own-row plane (bounce-back)
-  unsigned dst;         // byte offset in the stage
-  unsigned bytes;       // 0: this lane has no such copy
-  int dy, dz;           // source row offset
-  int esize;            // bytes per element of the field
-  int nb_pop;           // population read from a neighbour row unless that row is solid
+  const char *src_own;  // population blocks: the own-row plane (bounce-back)
+  unsigned dst;         // byte offset of the block in the stage
+  int esize;            // bytes per element; 0: this lane has no such block
+  int dy0, dz;          // source row offset of block row 0
+  int extra;            // rows beyond the tile's (halo blocks: 2)
+  int nb_pop;           // population block read from neighbour rows
 };
 
 template <class LAT, class ST, bool ODD, int PITCH>
-__device__ __forceinline__ RowCopy make_row_copy(const LatticeDev &L, int j) {
+__device__ __forceinline__ TileCopy make_tile_copy(const LatticeDev &L, int j) {
   using Lay = RowLayout<LAT, ST, ODD, PITCH>;
-  RowCopy c;
+  constexpr int nsig = ODD ? (LAT::D == 2 ? 1 : 3) : 1;
+  constexpr int nfb = LAT::D == 2 ? 1 : 3;  // field blocks: plane z (with halo rows), z - 1, z + 1
+  TileCopy c;
   const bool tv = L.has_deps != 0;
-  const int nfield = Lay::kEpsRows + (tv ? Lay::kDepsRows : 0);
-  const int ncopies = LAT::Q + Lay::kSigRows + nfield;
-  // whole stored rows (pitch nxp, a multiple of 8 elements: 16-byte sizes)
-  const unsigned nxp = (unsigned)L.nxp;
-  c.bytes = 0;
-  c.dy = c.dz = 0;
-  c.nb_pop = 0;
+  const int ncopies = LAT::Q + nsig + nfb * (tv ? 2 : 1);
+  c.esize = 0;
+  c.dy0 = c.dz = c.extra = c.nb_pop = 0;
   c.src = c.src_own = nullptr;
   c.dst = 0;
-  c.esize = 4;
   if (j >= ncopies) return c;
   if (j < LAT::Q) {
     int cy, cz;
@@ -192,60 +210,129 @@ __device__ __forceinline__ RowCopy make_row_copy(const LatticeDev &L, int j) {
     c.src_own = pop + j * plane_bytes;
     if (ODD && j != 0) {
       c.src = pop + opp_of(j) * plane_bytes;
-      c.dy = -cy;
+      c.dy0 = -cy;
       c.dz = -cz;
       c.nb_pop = 1;
     } else {
       c.src = c.src_own;
     }
     c.dst = (unsigned)(j * Lay::kPopBytes);
-    c.bytes = nxp * (unsigned)sizeof(ST);
     c.esize = (int)sizeof(ST);
-  } else if (j < LAT::Q + Lay::kSigRows) {
+  } else if (j < LAT::Q + nsig) {
     const int e = j - LAT::Q;
-    c.dy = ODD ? (LAT::D == 2 ? e : e % 3) - 1 : 0;
-    c.dz = ODD ? (LAT::D == 2 ? 0 : e / 3 - 1) : 0;
     c.src = reinterpret_cast<const char *>(L.sig_wr);
-    c.dst = (unsigned)(Lay::kSigOff + e * Lay::kSigBytes);
-    c.bytes = nxp * 2u;
     c.esize = 2;
+    if (ODD) {
+      c.dz = LAT::D == 2 ? 0 : e - 1;
+      c.dy0 = -1;
+      c.extra = 2;
+      c.dst = (unsigned)(Lay::kSigOff + e * 3 * Lay::kSigBytes);
+    } else {
+      c.dst = (unsigned)Lay::kSigOff;
+    }
   } else {
-    const int f = j - LAT::Q - Lay::kSigRows;
-    const bool is_deps = f >= Lay::kEpsRows;
-    const int e = is_deps ? f - Lay::kEpsRows : f;
-    c.dy = cross_dy<LAT>(e);
-    c.dz = cross_dz<LAT>(e);
+    const int f = j - LAT::Q - nsig;
+    const bool is_deps = f >= nfb;
+    const int e = is_deps ? f - nfb : f;
     c.src = static_cast<const char *>(is_deps ? L.deps : L.eps);
-    c.dst = (unsigned)((is_deps ? Lay::kDepsOff : Lay::kEpsOff) + e * Lay::kRowBytes);
-    c.bytes = nxp * 4u;
     c.esize = 4;
+    const unsigned off = (unsigned)(is_deps ? Lay::kDepsOff : Lay::kEpsOff);
+    if (e == 0) {
+      c.dy0 = -1;
+      c.extra = 2;
+      c.dst = off;
+    } else {
+      c.dz = e == 1 ? -1 : 1;
+      c.dst = off + (unsigned)((e + 2) * Lay::kRowBytes);
+    }
   }
   return c;
 }
 
-// Is row (y, z) a wall layer?
-__device__ __forceinline__ bool wall_row(unsigned walls, int y, int z, int ny, int nz) {
-  return ((walls & 2u) && (y <= 0 || y >= ny - 1)) || ((walls & 4u) && (z <= 0 || z >= nz - 1));
+// Bytes one lane's block of a tile of nr rows copies.
+__device__ __forceinline__ unsigned tile_copy_bytes(const TileCopy &c, int nr, int nxp) {
+  return c.esize ? (unsigned)((nr + c.extra) * nxp * c.esize) : 0u;
 }
 
-// Issue copy c of row (y, z) into `stage`, completing on `bar`.
-__device__ __forceinline__ void issue_copy(const RowCopy &c, unsigned char *stage, unsigned long long *bar,
-                                           int y, int z, int ny, int nz, int nxp, unsigned walls) {
-  if (!c.bytes) return;
-  int dy = c.dy, dz = c.dz;
-  const char *src = c.src;
-  if (c.nb_pop && walls && wall_row(walls, y + dy, z + dz, ny, nz)) {
-    // halfway bounce-back: the population comes from the own row
-    dy = 0;
-    dz = 0;
-    src = c.src_own;
+// Issue the copies of block c for the tile (y0, z, nr) into `stage`,
+// completing on `bar`: block row k lands at k * dst_row_bytes (the stored
+// row size nxp * esize, or the slot size PITCH * esize of one-row tiles).
+// Source rows inside the lattice, in one plane, with no wall substitution
+// (every block but those at a periodic edge or next to a wall) go as one
+// copy (or one per row when the two row sizes differ); the others are
+// split into runs of rows consecutive in both places.
+__device__ __forceinline__ void issue_tile_copy(const TileCopy &c, unsigned char *stage, unsigned long long *bar,
+                                                int y0, int z, int nr, int ny, int nz, int nxp, unsigned walls,
+                                                int dst_pitch) {
+  if (!c.esize) return;
+  const int n = nr + c.extra;
+  const unsigned row_bytes = (unsigned)(nxp * c.esize);
+  const unsigned dst_row_bytes = (unsigned)(dst_pitch * c.esize);
+  const bool merge = dst_row_bytes == row_bytes;
+  const int ys = y0 + c.dy0, zs = z + c.dz;
+  const bool inside = ys >= 0 && ys + n <= ny && zs >= 0 && zs < nz;
+  const bool sub = c.nb_pop && (((walls & 2u) && (ys <= 0 || ys + n - 1 >= ny - 1)) ||
+                                ((walls & 4u) && (zs <= 0 || zs >= nz - 1)));
+  if (inside && !sub) {
+    const char *src = c.src + ((long long)zs * ny + ys) * row_bytes;
+    unsigned char *dst = stage + c.dst;
+    if (merge) {
+      bulk_g2s(dst, src, (unsigned)n * row_bytes, bar);
+    } else {
+      for (int k = 0; k < n; ++k) bulk_g2s(dst + k * dst_row_bytes, src + k * row_bytes, row_bytes, bar);
+    }
+    return;
   }
-  const int yy = wrapi(y + dy, ny), zz = wrapi(z + dz, nz);
-  bulk_g2s(stage + c.dst, src + (long long)((zz * ny + yy) * nxp) * c.esize, c.bytes, bar);
+  const char *run_src = nullptr;
+  long long run_row = 0;
+  int run_k = 0, run_len = 0;
+  for (int k = 0; k < n; ++k) {
+    int yy = ys + k, zz = zs;
+    const char *src = c.src;
+    if (c.nb_pop && walls && wall_row(walls, yy, zz, ny, nz)) {
+      // halfway bounce-back: the population comes from the own row
+      yy = y0 + k;
+      zz = z;
+      src = c.src_own;
+    }
+    const long long row = (long long)wrapi(zz, nz) * ny + wrapi(yy, ny);
+    if (run_len && merge && src == run_src && row == run_row + run_len) {
+      ++run_len;
+      continue;
+    }
+    if (run_len)
+      bulk_g2s(stage + c.dst + run_k * dst_row_bytes, run_src + run_row * row_bytes, run_len * row_bytes, bar);
+    run_src = src;
+    run_row = row;
+    run_k = k;
+    run_len = 1;
+  }
+  if (run_len)
+    bulk_g2s(stage + c.dst + run_k * dst_row_bytes, run_src + run_row * row_bytes, run_len * row_bytes, bar);
 }
 
-// Update the 32-cell chunk [x0, x0 + 32) of one staged row (one cell per
-// lane).
+// The row contexts of the tile (y0, z, nr), written by the producer warp
+// (lanes in parallel) into rc[0 .. nr).
+__device__ __forceinline__ void fill_row_ctx(RowCtx *rc, int y0, int z, int nr, int ny, int nz, int nxp,
+                                             unsigned walls, int lane) {
+  for (int idx = lane; idx < nr * 9; idx += 32) {
+    const int t = idx / 9, e = idx - t * 9;
+    const int dy = e % 3 - 1, dz = e / 3 - 1;
+    rc[t].base[dz + 1][dy + 1] = (wrapi(z + dz, nz) * ny + wrapi(y0 + t + dy, ny)) * nxp;
+  }
+  if (lane < nr) {
+    unsigned solid = 0;
+    if (walls) {
+#pragma unroll
+      for (int e = 0; e < 9; ++e)
+        if (wall_row(walls, y0 + lane + e % 3 - 1, z + e / 3 - 1, ny, nz)) solid |= 1u << e;
+    }
+    rc[lane].solid = solid;
+  }
+}
+
+// Update the 32-cell chunk [x0, x0 + 32) of row t of a staged tile (one
+// cell per lane).
 // RS: the step after a phi refresh decodes with the old shift and encodes
 // with the new one ("reshift").  0: no refresh pending, 1: pending (both
 // known at launch), 2: read it from the descriptor.
@@ -253,8 +340,9 @@ __device__ __forceinline__ void issue_copy(const RowCopy &c, unsigned char *stag
 // memory (row i holds f*_i at the position of its storage cell in the
 // destination row) instead of straight to global memory; a storer warp
 // writes the rows back with bulk copies.
-template <class LAT, class ST, bool ODD, bool RED, bool WALLS, int PITCH, int RS = 2, bool OUTS = false>
-__device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsigned char *stage,
+template <class LAT, class ST, bool ODD, bool RED, bool WALLS, int PITCH, int RS = 2, bool OUTS = false,
+          bool TILED = true>
+__device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsigned char *stage, int t,
                                                  const RowCtx &rc, long long n, float dn, float dn_force,
                                                  int x, RedAcc &acc, unsigned char *ostage = nullptr) {
   using Lay = RowLayout<LAT, ST, ODD, PITCH>;
@@ -269,10 +357,22 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
   // balance through the rest population (step 8 below)
   constexpr bool kMassFix = sizeof(ST) == 4;
   const int nx = L.nx;
-  const ST *prow = reinterpret_cast<const ST *>(stage);
-  const __half *srow = reinterpret_cast<const __half *>(stage + Lay::kSigOff);
-  const float *erow = reinterpret_cast<const float *>(stage + Lay::kEpsOff);
-  const float *drow = reinterpret_cast<const float *>(stage + Lay::kDepsOff);
+  // smem row pitch and row of the tile: TILED, nxp and t (rows of the tile
+  // copied together land at their stored pitch); else one row per stage at
+  // the compile-time pitch PITCH (every offset below an immediate)
+  const int sp = TILED ? L.nxp : PITCH, tt = TILED ? t : 0;
+  // row t of the staged tile: population block i at prow + i PITCH; the
+  // shift of row (y + dy, z + dz) at srow[sig_block(dz) 3 PITCH + dy sp]
+  // (odd steps) or srow (even steps); phi_ref of row (y + dy, z) at
+  // e0[dy sp], of rows (y, z -+ 1) at ezm, ezp (d_t phi likewise)
+  const ST *prow = reinterpret_cast<const ST *>(stage) + tt * sp;
+  const __half *srow = reinterpret_cast<const __half *>(stage + Lay::kSigOff) + (ODD ? tt + 1 : tt) * sp;
+  const float *e0 = reinterpret_cast<const float *>(stage + Lay::kEpsOff) + (tt + 1) * sp;
+  const float *ezm = reinterpret_cast<const float *>(stage + Lay::kEpsOff) + 3 * PITCH + tt * sp;
+  const float *ezp = ezm + PITCH;
+  const float *d0 = reinterpret_cast<const float *>(stage + Lay::kDepsOff) + (tt + 1) * sp;
+  const float *dzm = reinterpret_cast<const float *>(stage + Lay::kDepsOff) + 3 * PITCH + tt * sp;
+  const float *dzp = dzm + PITCH;
   const bool tv = L.has_deps != 0;
   const float rho0 = L.rho0f;
   const float inv_scale = L.inv_scale, scale = L.scale;
@@ -289,9 +389,10 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
   const float cf3 = L.cf3f, cf9 = L.cf9f;
   const unsigned qa = L.quad_axes;
 
-#define EPS_AT(dy, dz, xx) erow[cross_index<LAT>((dy), (dz)) * PITCH + (xx)]
-#define DEPS_AT(dy, dz, xx) drow[cross_index<LAT>((dy), (dz)) * PITCH + (xx)]
-#define SIG_AT(dy, dz, xx) __half2float(srow[sig_index<LAT, ODD>((dy), (dz)) * PITCH + (xx)])
+#define EPS_AT(dy, dz, xx) ((dz) == 0 ? e0[(dy) * sp + (xx)] : ((dz) < 0 ? ezm[xx] : ezp[xx]))
+#define DEPS_AT(dy, dz, xx) ((dz) == 0 ? d0[(dy) * sp + (xx)] : ((dz) < 0 ? dzm[xx] : dzp[xx]))
+#define SIG_AT(dy, dz, xx) \
+  __half2float(ODD ? srow[sig_block<LAT>(dz) * 3 * PITCH + (dy) * sp + (xx)] : srow[xx])
   // slot of population i read from / written to this cell's own memory?
 #define OWN_SRC(i) (!ODD || (i) == 0 || (WALLS && ((rc.solid >> ((1 - LAT::c((i), 2)) * 3 + (1 - LAT::c((i), 1)))) & 1u)))
 #define OWN_DST(i) (!ODD || (i) == 0 || (WALLS && ((rc.solid >> ((1 + LAT::c((i), 2)) * 3 + (1 + LAT::c((i), 1)))) & 1u)))
@@ -445,6 +546,7 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
   const float enc_own = reshift ? fmaf(-rho0, sig_own, s_x) : 0.f;
   SRng rng((unsigned)cell, n);
   const bool sr = L.fp16_nearest == 0;
+  ST *orow = OUTS ? reinterpret_cast<ST *>(ostage) + tt * sp : nullptr;
   // encode population i (compile-time index) with post-collision deviation
   // DSTAR (storage units): P_ = its slot, V_ = the value to store against
   // the shift of the cell whose memory holds it
@@ -456,7 +558,7 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
     const float ds_ = (DSTAR);                                                                     \
     if (OWN_DST(i)) {                                                                              \
       V_ = reshift ? fmaf(enc_own, sc, ds_) : ds_;                                                 \
-      P_ = OUTS ? reinterpret_cast<ST *>(ostage) + (i) * PITCH + x : (pop + opp_of(i) * plane) + cell; \
+      P_ = OUTS ? orow + (i) * PITCH + x : (pop + opp_of(i) * plane) + cell;                   \
     } else {                                                                                       \
       const int xm_ = xs[1 + cx_];                                                                 \
       float enc_;                                                                                  \
@@ -465,7 +567,7 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
       else                                                                                         \
         enc_ = fmaf(-rho0, SIG_AT(cy_, cz_, xm_), s_x);                                            \
       V_ = fmaf(enc_, sc, ds_);                                                                    \
-      P_ = OUTS ? reinterpret_cast<ST *>(ostage) + (i) * PITCH + xm_                               \
+      P_ = OUTS ? orow + (i) * PITCH + xm_                                                        \
                 : (pop + (i) * plane) + (rc.base[1 + cz_][1 + cy_] + xm_);                         \
     }                                                                                              \
   }
@@ -547,6 +649,12 @@ __device__ __forceinline__ void update_row_chunk(const LatticeDev &L, const unsi
 #undef OWN_DST
 }
 
+}  // namespace lbm
+
+#include "step_row_pair.cuh"
+
+namespace lbm {
+
 __device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -580,6 +688,44 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// Write population i's output block of the tile (y0, z, nr) back (storer
+// lane i; block row t at t * src_pitch elements): row t goes to row (y0 + t
+// + c_iy, z + c_iz) of plane i at odd steps (i > 0) unless that row is a
+// wall layer, else to the own row of plane opp(i); one bulk store per run of
+// rows consecutive in both places.
+template <class LAT, class ST, bool ODD>
+__device__ __forceinline__ void store_tile_block(const LatticeDev &L, const unsigned char *oblock, int i, int cy,
+                                                 int cz, int y0, int z, int nr, int src_pitch) {
+  const int ny = L.ny, nz = L.nz, nxp = L.nxp;
+  const unsigned walls = L.walls;
+  const long long plane_bytes = L.plane * (long long)sizeof(ST);
+  char *pop = static_cast<char *>(L.pop);
+  const unsigned row_bytes = (unsigned)nxp * (unsigned)sizeof(ST);
+  const unsigned src_row_bytes = (unsigned)src_pitch * (unsigned)sizeof(ST);
+  const bool merge = src_row_bytes == row_bytes;
+  const bool moves = ODD && i != 0;
+  char *run_dst = nullptr;
+  int run_t = 0, run_len = 0;
+  long long run_row = 0;
+  for (int t = 0; t < nr; ++t) {
+    const int y = y0 + t;
+    const bool to_nb = moves && !(walls && wall_row(walls, y + cy, z + cz, ny, nz));
+    const int yy = to_nb ? wrapi(y + cy, ny) : y, zz = to_nb ? wrapi(z + cz, nz) : z;
+    char *dst = pop + (to_nb ? i : opp_of(i)) * plane_bytes;
+    const long long row = (long long)zz * ny + yy;
+    if (run_len && merge && dst == run_dst && row == run_row + run_len) {
+      ++run_len;
+      continue;
+    }
+    if (run_len) bulk_s2g(run_dst + run_row * row_bytes, oblock + run_t * src_row_bytes, run_len * row_bytes);
+    run_dst = dst;
+    run_row = row;
+    run_t = t;
+    run_len = 1;
+  }
+  if (run_len) bulk_s2g(run_dst + run_row * row_bytes, oblock + run_t * src_row_bytes, run_len * row_bytes);
+}
+
 // Shape of one row kernel instantiation.  FP16 rows are written back
 // through two output stages in shared memory by bulk copies (fewer
 // instructions per cell than scattered 2-byte stores: measured -8 % on the
@@ -598,39 +744,46 @@ struct RowCfg {
   static constexpr int kInOnly = kBudget / kIn;
   static constexpr int kNS = kOuts ? (kInWithOut < kMaxIn ? kInWithOut : kMaxIn) : (kInOnly < kMaxIn ? kInOnly : kMaxIn);
   static constexpr int kNOut = kOuts ? 2 : 0;
-  static constexpr int kConsumers = row_consumers<MINB>();
+  static constexpr int kConsumers = row_consumers<MINB, row_pair_lattice<LAT, ST>()>();
   static constexpr int kThreads = (kConsumers + (kOuts ? 2 : 1)) * 32;
   static constexpr int kSmem = kNS * kIn + kNOut * kOut;
 };
 
 // Warp-specialised row kernel.  Warp kConsumerWarps is the producer: it
-// stages row j into stage j % NSTAGE once the consumers have released the
-// row that used it before (empty barrier), arming the full barrier with the
-// byte count of the copies.  Each producer lane owns two of the row's copies,
-// set up once per launch, so staging a row costs a few instructions per lane
+// stages tile j into stage j % NSTAGE once the consumers have released the
+// tile that used it before (empty barrier), writes the tile's row contexts
+// and arms the full barrier with the byte count of the copies.  Each
+// producer lane owns up to two blocks of the tile's copies, set up once per
+// launch, so staging a tile costs a few instructions per lane per row
 // besides the copies.  The consumer warps wait on the full barrier, update
-// their cells and release the stage, one arrival per warp.
-// NOUT > 0: the consumers write the updated row into output stage j % NOUT
+// their chunks of the tile's rows and release the stage, one arrival per
+// warp.
+// NOUT > 0: the consumers write the updated tile into output stage j % NOUT
 // (after the storer has released it: oempty), then arrive on ofull; the
-// storer warp (kConsumerWarps + 1) waits on ofull, copies the Q output rows
+// storer warp (kConsumerWarps + 1) waits on ofull, copies the Q output blocks
 // to their destination rows with bulk copies (lane i: population i), waits
 // until the copies have read the stage and releases it.  No block-wide
 // barrier is taken inside the loop.
-// TUNED = false: row_consumers<MINB>() consumer warps and MAXSTAGE input
-// stages, compile-time constants (the default shape).  TUNED = true: the
-// launch chooses the consumer warps (blockDim.x / 32 minus the producer and
-// storer warps, at most row_consumers<MINB>()) and the input stages
-// `nstage` (2 <= nstage <= MAXSTAGE), the autotuner's knobs; this generic
-// form costs 2-5 % at the default shape (measured), so it runs only when a
-// tuned shape differs from the default, and only for plain steps.
+// TUNED = false: row_consumers() consumer warps and MAXSTAGE input stages,
+// compile-time constants (the default shape).  TUNED = true: the launch
+// chooses the consumer warps (blockDim.x / 32 minus the producer and storer
+// warps, at most the default) and the input stages `nstage` (2 <= nstage <=
+// MAXSTAGE), the autotuner's knobs; this generic form costs 2-5 % at the
+// default shape (measured), so it runs only when a tuned shape differs from
+// the default, and only for plain steps.
 template <class LAT, class ST, bool ODD, bool RED, bool WALLS, int PITCH, int MAXSTAGE, int MINB, int RS, int NOUT,
-          bool TUNED = false>
-__global__ void __launch_bounds__((row_consumers<MINB>() + (NOUT ? 2 : 1)) * 32, MINB)
+          bool TILED, bool TUNED = false>
+__global__ void __launch_bounds__((row_consumers<MINB, row_pair_lattice<LAT, ST>()>() + (NOUT ? 2 : 1)) * 32, MINB)
     step_row_kernel(const LatticeDev *__restrict__ Lp, int k, int nstage) {
   constexpr int Q = LAT::Q;
   using Lay = RowLayout<LAT, ST, ODD, PITCH>;
   constexpr int kOutBytes = (Q * PITCH * (int)sizeof(ST) + 127) / 128 * 128;
-  const int kConsumerWarps = TUNED ? (int)(blockDim.x >> 5) - (NOUT ? 2 : 1) : row_consumers<MINB>();
+  // FP16 plain steps of D2Q9/D3Q19 update two adjacent cells per lane
+  // (update_row_pair: bit-identical results, fewer instructions per cell)
+  constexpr bool kPair = row_pair_lattice<LAT, ST>() && !RED && RS == 0;
+  constexpr int kChunk = kPair ? 64 : 32;
+  const int kConsumerWarps =
+      TUNED ? (int)(blockDim.x >> 5) - (NOUT ? 2 : 1) : row_consumers<MINB, row_pair_lattice<LAT, ST>()>();
   const int NSTAGE = TUNED ? nstage : MAXSTAGE;
   const int kInRegion = NSTAGE * RowLayout<LAT, ST, true, PITCH>::kStageBytes;
   __shared__ LatticeDev Ls;
@@ -638,7 +791,7 @@ __global__ void __launch_bounds__((row_consumers<MINB>() + (NOUT ? 2 : 1)) * 32,
   __shared__ alignas(8) unsigned long long empty[MAXSTAGE];
   __shared__ alignas(8) unsigned long long ofull[NOUT > 0 ? NOUT : 1];
   __shared__ alignas(8) unsigned long long oempty[NOUT > 0 ? NOUT : 1];
-  __shared__ RowCtx ctx[MAXSTAGE];
+  __shared__ RowCtx ctx[MAXSTAGE][TILED ? kMaxTileRows : 1];
   __shared__ volatile int abort_flag;
   extern __shared__ __align__(128) unsigned char stages[];
   const int tid = threadIdx.x;
@@ -663,9 +816,15 @@ __global__ void __launch_bounds__((row_consumers<MINB>() + (NOUT ? 2 : 1)) * 32,
   __syncthreads();
   const LatticeDev &L = Ls;
   const bool wy = (L.walls & 2u) != 0, wz = (L.walls & 4u) != 0;
-  const int y0 = wy ? 1 : 0, nyf = wy ? L.ny - 2 : L.ny;
-  const int z0 = wz ? 1 : 0, nzf = wz ? L.nz - 2 : L.nz;
-  const int nrows = nyf * nzf;
+  const int y_first = wy ? 1 : 0, nyf = wy ? L.ny - 2 : L.ny;
+  const int z_first = wz ? 1 : 0, nzf = wz ? L.nz - 2 : L.nz;
+  // tiles of R rows of one plane: tile it is rows y_first + (it % tpp) R ..
+  // of plane z_first + it / tpp (the plane's last tile may be shorter);
+  // TILED = false: one row per tile, staged at the compile-time pitch
+  const int R = TILED ? tile_rows(PITCH, L.nxp) : 1;
+  const int spitch = TILED ? L.nxp : PITCH;
+  const int tpp = (nyf + R - 1) / R;
+  const int ntiles = tpp * nzf;
   const unsigned limit = L.wait_limit;
   RedAcc acc;
 #pragma unroll
@@ -676,21 +835,22 @@ __global__ void __launch_bounds__((row_consumers<MINB>() + (NOUT ? 2 : 1)) * 32,
     const bool withhold = L.withhold_copies != 0;
     const int ny = L.ny, nz = L.nz, nxp = L.nxp;
     const unsigned walls = L.walls;
-    const RowCopy c0 = make_row_copy<LAT, ST, ODD, PITCH>(L, lane);
-    const RowCopy c1 = make_row_copy<LAT, ST, ODD, PITCH>(L, lane + 32);
-    const unsigned row_bytes = (unsigned)__reduce_add_sync(0xffffffffu, c0.bytes + c1.bytes);
-    // row r = blockIdx.x + j * gridDim.x is (y0 + r % nyf, z0 + r / nyf); the
-    // step from one row of the block to the next is carried incrementally
-    const int step_y = (int)(gridDim.x % (unsigned)nyf), step_z = (int)(gridDim.x / (unsigned)nyf);
-    int ry = (int)(blockIdx.x % (unsigned)nyf), rz = (int)(blockIdx.x / (unsigned)nyf);
-    // lanes 0..8: the row context entry (dy, dz) = (lane % 3 - 1, lane / 3 - 1)
-    const int cdy = lane % 3 - 1, cdz = lane / 3 - 1;
-    int issued_upto = -1;  // last row index j whose copies were issued
+    const TileCopy c0 = make_tile_copy<LAT, ST, ODD, PITCH>(L, lane);
+    const TileCopy c1 = make_tile_copy<LAT, ST, ODD, PITCH>(L, lane + 32);
+    // bytes of a tile of nr rows: per_row * nr + fixed
+    const unsigned per_row = __reduce_add_sync(0xffffffffu, tile_copy_bytes(c0, 1, nxp) - tile_copy_bytes(c0, 0, nxp) +
+                                                               tile_copy_bytes(c1, 1, nxp) - tile_copy_bytes(c1, 0, nxp));
+    const unsigned fixed = __reduce_add_sync(0xffffffffu, tile_copy_bytes(c0, 0, nxp) + tile_copy_bytes(c1, 0, nxp));
+    // tile it = blockIdx.x + j G is (ty, tz) = (it % tpp, it / tpp), carried
+    // incrementally from one tile of the block to the next
+    const int step_y = (int)(gridDim.x % (unsigned)tpp), step_z = (int)(gridDim.x / (unsigned)tpp);
+    int ty = (int)(blockIdx.x % (unsigned)tpp), tz = (int)(blockIdx.x / (unsigned)tpp);
+    int issued_upto = -1;  // last tile index j whose copies were issued
     int j = 0;
-    for (int r = blockIdx.x; r < nrows; r += gridDim.x, ++j) {
+    for (int it = blockIdx.x; it < ntiles; it += gridDim.x, ++j) {
       const int s = j % NSTAGE;
       if (j >= NSTAGE) {
-        // the consumers released row j - NSTAGE from this stage
+        // the consumers released tile j - NSTAGE from this stage
         if (!mbar_wait_or_abort(&empty[s], (unsigned)(((j / NSTAGE) - 1) & 1), limit, &abort_flag)) {
           if (lane == 0 && !abort_flag) {
             abort_flag = 1;
@@ -699,27 +859,25 @@ __global__ void __launch_bounds__((row_consumers<MINB>() + (NOUT ? 2 : 1)) * 32,
           break;
         }
       }
-      const int y = y0 + ry, z = z0 + rz;
-      const bool sol = lane < 9 && wall_row(walls, y + cdy, z + cdz, ny, nz);
-      const unsigned solid = __ballot_sync(0xffffffffu, sol) & 0x1ffu;
-      if (lane < 9) ctx[s].base[cdz + 1][cdy + 1] = (wrapi(z + cdz, nz) * ny + wrapi(y + cdy, ny)) * nxp;
-      if (lane == 0) ctx[s].solid = solid;
+      const int y0 = y_first + ty * R, z = z_first + tz, nr = min(R, nyf - ty * R);
+      ty += step_y;
+      tz += step_z;
+      if (ty >= tpp) {
+        ty -= tpp;
+        ++tz;
+      }
+      fill_row_ctx(ctx[s], y0, z, nr, ny, nz, nxp, walls, lane);
+      const unsigned bytes = per_row * (unsigned)nr + fixed;
       __syncwarp();
       if (!withhold) {
-        if (lane == 0) mbar_arrive_expect_tx(&full[s], row_bytes);
+        if (lane == 0) mbar_arrive_expect_tx(&full[s], bytes);
         __syncwarp();
         unsigned char *stage = stages + s * Lay::kStageBytes;
-        issue_copy(c0, stage, &full[s], y, z, ny, nz, nxp, walls);
-        issue_copy(c1, stage, &full[s], y, z, ny, nz, nxp, walls);
+        issue_tile_copy(c0, stage, &full[s], y0, z, nr, ny, nz, nxp, walls, spitch);
+        issue_tile_copy(c1, stage, &full[s], y0, z, nr, ny, nz, nxp, walls, spitch);
         issued_upto = j;
       }
       __syncwarp();
-      ry += step_y;
-      rz += step_z;
-      if (ry >= nyf) {
-        ry -= nyf;
-        ++rz;
-      }
     }
     if (abort_flag && lane == 0) {
       // drain: wait (full limit) for every stage whose copies may be in flight
@@ -727,19 +885,11 @@ __global__ void __launch_bounds__((row_consumers<MINB>() + (NOUT ? 2 : 1)) * 32,
         if (jj >= 0) mbar_wait_bounded(&full[jj % NSTAGE], (unsigned)((jj / NSTAGE) & 1));
     }
   } else if (NOUT > 0 && warp == kConsumerWarps + 1) {
-    // ---------------- storer warp: lane i writes population i's row back
-    const int ny = L.ny, nz = L.nz, nxp = L.nxp;
-    const unsigned walls = L.walls;
-    const long long plane_bytes = L.plane * (long long)sizeof(ST);
-    const char *pop = static_cast<const char *>(L.pop);
-    const unsigned row_bytes = (unsigned)nxp * (unsigned)sizeof(ST);
+    // ---------------- storer warp: lane i writes population i's block back
     int cy = 0, cz = 0;
     if (lane < Q) dir_yz<LAT>(lane, cy, cz);
-    const bool moves = ODD && lane != 0;
-    const int step_y = (int)(gridDim.x % (unsigned)nyf), step_z = (int)(gridDim.x / (unsigned)nyf);
-    int ry = (int)(blockIdx.x % (unsigned)nyf), rz = (int)(blockIdx.x / (unsigned)nyf);
     int j = 0;
-    for (int r = blockIdx.x; r < nrows; r += gridDim.x, ++j) {
+    for (int it = blockIdx.x; it < ntiles; it += gridDim.x, ++j) {
       const int o = j % NOUT;
       if (!mbar_wait_or_abort(&ofull[o], (unsigned)((j / NOUT) & 1), limit, &abort_flag)) {
         if (lane == 0 && !abort_flag) {
@@ -748,26 +898,16 @@ __global__ void __launch_bounds__((row_consumers<MINB>() + (NOUT ? 2 : 1)) * 32,
         }
         break;
       }
-      const int y = y0 + ry, z = z0 + rz;
+      const int tz = it / tpp, ty = it - tz * tpp;
+      const int y0 = y_first + ty * R, z = z_first + tz, nr = min(R, nyf - ty * R);
       if (lane < Q) {
-        // even step, rest population, or a target row in a wall layer: the
-        // own row, plane opp(i); else plane i of row (y + c_iy, z + c_iz)
-        const bool to_nb = moves && !(walls && wall_row(walls, y + cy, z + cz, ny, nz));
-        const int yy = to_nb ? wrapi(y + cy, ny) : y, zz = to_nb ? wrapi(z + cz, nz) : z;
-        const int pl = to_nb ? lane : opp_of(lane);
-        char *dst = const_cast<char *>(pop) + pl * plane_bytes + (long long)((zz * ny + yy) * nxp) * sizeof(ST);
-        bulk_s2g(dst, stages + kInRegion + o * kOutBytes + lane * PITCH * (int)sizeof(ST), row_bytes);
+        store_tile_block<LAT, ST, ODD>(L, stages + kInRegion + o * kOutBytes + lane * PITCH * (int)sizeof(ST), lane,
+                                       cy, cz, y0, z, nr, spitch);
         bulk_commit();
         bulk_wait_read_all();
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&oempty[o]);
-      ry += step_y;
-      rz += step_z;
-      if (ry >= nyf) {
-        ry -= nyf;
-        ++rz;
-      }
     }
     if (lane < Q) bulk_wait_all();
   } else {
@@ -775,8 +915,10 @@ __global__ void __launch_bounds__((row_consumers<MINB>() + (NOUT ? 2 : 1)) * 32,
     const long long n = L.n + k;
     // steps since the phi and force references, converted once per launch
     const float dn = (float)(n - L.n_eps), dn_force = (float)(n - L.n_force);
+    const int ncr = (L.nx + kChunk - 1) / kChunk;  // chunks per row
+    int rot = 0;  // chunks dealt so far, modulo the consumer warps (all warps agree)
     int j = 0;
-    for (int r = blockIdx.x; r < nrows; r += gridDim.x, ++j) {
+    for (int it = blockIdx.x; it < ntiles; it += gridDim.x, ++j) {
       const int s = j % NSTAGE;
       if (!mbar_wait_or_abort(&full[s], (unsigned)((j / NSTAGE) & 1), limit, &abort_flag)) {
         if (lane == 0 && !abort_flag) {
@@ -788,7 +930,7 @@ __global__ void __launch_bounds__((row_consumers<MINB>() + (NOUT ? 2 : 1)) * 32,
       unsigned char *ostage = nullptr;
       if (NOUT > 0) {
         const int o = j % NOUT;
-        // the storer has finished reading row j - NOUT from this output stage
+        // the storer has finished reading tile j - NOUT from this output stage
         if (j >= NOUT && !mbar_wait_or_abort(&oempty[o], (unsigned)(((j / NOUT) - 1) & 1), limit, &abort_flag)) {
           if (lane == 0 && !abort_flag) {
             abort_flag = 1;
@@ -798,13 +940,23 @@ __global__ void __launch_bounds__((row_consumers<MINB>() + (NOUT ? 2 : 1)) * 32,
         }
         ostage = stages + kInRegion + o * kOutBytes;
       }
-      // 32-cell chunks of the row, dealt round-robin to the consumer warps
-      // across rows so that every warp gets the same share
-      const int nchunks = (L.nx + 31) >> 5;
-      const int first = (warp - (int)(((long long)j * nchunks) % kConsumerWarps) + kConsumerWarps) % kConsumerWarps;
-      for (int c = first; c < nchunks; c += kConsumerWarps)
-        update_row_chunk<LAT, ST, ODD, RED, WALLS, PITCH, RS, (NOUT > 0)>(
-            L, stages + s * Lay::kStageBytes, ctx[s], n, dn, dn_force, (c << 5) + lane, acc, ostage);
+      const int tz = it / tpp, ty = it - tz * tpp;
+      const int nr = min(R, nyf - ty * R);
+      // the tile's chunks (row t, chunk c of the row), dealt round-robin to
+      // the consumer warps across tiles so that every warp gets the same share
+      const int nch = nr * ncr;
+      const int first = (warp - rot + kConsumerWarps) % kConsumerWarps;
+      const unsigned char *stage = stages + s * Lay::kStageBytes;
+      for (int c = first; c < nch; c += kConsumerWarps) {
+        const int t = c / ncr, xc = c - t * ncr;
+        if constexpr (kPair)
+          update_row_pair<LAT, ODD, WALLS, PITCH, (NOUT > 0), TILED>(L, stage, t, ctx[s][t], n, dn, dn_force,
+                                                                     xc * kChunk + 2 * lane, ostage);
+        else
+          update_row_chunk<LAT, ST, ODD, RED, WALLS, PITCH, RS, (NOUT > 0), TILED>(
+              L, stage, t, ctx[s][t], n, dn, dn_force, xc * kChunk + lane, acc, ostage);
+      }
+      rot = (rot + nch) % kConsumerWarps;
       if (NOUT > 0) fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) {
@@ -823,8 +975,9 @@ namespace lbm {
 
 // Host side: launch and planning of the row kernel for one lattice type.
 // ls.row encodes the variant: bit 0 set = in use, bit 1 = walls, bit 2 =
-// pitch 512 (else 256).
-template <class LAT, class ST, bool W, int P, int MINB, int RS>
+// pitch 512 (else 256), bit 3 = tiles of several rows (rows of at most half
+// the pitch).
+template <class LAT, class ST, bool W, int P, int MINB, int RS, bool TL>
 cudaError_t launch_row_rs(const LatticeDev *L_dev, bool odd, bool red, int k, const StepLaunch &ls,
                           cudaStream_t s) {
   using C = RowCfg<LAT, ST, P, MINB>;
@@ -837,51 +990,55 @@ cudaError_t launch_row_rs(const LatticeDev *L_dev, bool odd, bool red, int k, co
   if (RS == 0 && !red && (nc != C::kConsumers || ns != NS)) {
     const dim3 block((nc + (NO ? 2 : 1)) * 32);
     const int smem = ns * C::kIn + NO * C::kOut;
-    if (odd) step_row_kernel<LAT, ST, true, false, W, P, NS, MINB, RS, NO, true><<<grid, block, smem, s>>>(L_dev, k, ns);
-    else step_row_kernel<LAT, ST, false, false, W, P, NS, MINB, RS, NO, true><<<grid, block, smem, s>>>(L_dev, k, ns);
+    if (odd) step_row_kernel<LAT, ST, true, false, W, P, NS, MINB, RS, NO, TL, true><<<grid, block, smem, s>>>(L_dev, k, ns);
+    else step_row_kernel<LAT, ST, false, false, W, P, NS, MINB, RS, NO, TL, true><<<grid, block, smem, s>>>(L_dev, k, ns);
     return cudaGetLastError();
   }
   const dim3 block(C::kThreads);
   const int smem = C::kSmem;
   if (odd) {
-    if (red) step_row_kernel<LAT, ST, true, true, W, P, NS, MINB, RS, NO><<<grid, block, smem, s>>>(L_dev, k, ns);
-    else step_row_kernel<LAT, ST, true, false, W, P, NS, MINB, RS, NO><<<grid, block, smem, s>>>(L_dev, k, ns);
+    if (red) step_row_kernel<LAT, ST, true, true, W, P, NS, MINB, RS, NO, TL><<<grid, block, smem, s>>>(L_dev, k, ns);
+    else step_row_kernel<LAT, ST, true, false, W, P, NS, MINB, RS, NO, TL><<<grid, block, smem, s>>>(L_dev, k, ns);
   } else {
-    if (red) step_row_kernel<LAT, ST, false, true, W, P, NS, MINB, RS, NO><<<grid, block, smem, s>>>(L_dev, k, ns);
-    else step_row_kernel<LAT, ST, false, false, W, P, NS, MINB, RS, NO><<<grid, block, smem, s>>>(L_dev, k, ns);
+    if (red) step_row_kernel<LAT, ST, false, true, W, P, NS, MINB, RS, NO, TL><<<grid, block, smem, s>>>(L_dev, k, ns);
+    else step_row_kernel<LAT, ST, false, false, W, P, NS, MINB, RS, NO, TL><<<grid, block, smem, s>>>(L_dev, k, ns);
   }
   return cudaGetLastError();
 }
 
 // red: bit 0 a check step, bit 1 the step decodes with the shift of the
 // previous phi (the first step after a refresh)
-template <class LAT, class ST, bool W, int P, int MINB>
+template <class LAT, class ST, bool W, int P, int MINB, bool TL>
 cudaError_t launch_row_v(const LatticeDev *L_dev, bool odd, int red, int k, const StepLaunch &ls,
                          cudaStream_t s) {
-  if (red & 2) return launch_row_rs<LAT, ST, W, P, MINB, 1>(L_dev, odd, (red & 1) != 0, k, ls, s);
-  return launch_row_rs<LAT, ST, W, P, MINB, 0>(L_dev, odd, (red & 1) != 0, k, ls, s);
+  if (red & 2) return launch_row_rs<LAT, ST, W, P, MINB, 1, TL>(L_dev, odd, (red & 1) != 0, k, ls, s);
+  return launch_row_rs<LAT, ST, W, P, MINB, 0, TL>(L_dev, odd, (red & 1) != 0, k, ls, s);
 }
 
 template <class LAT, class ST, int MINB>
 cudaError_t launch_row_t(const LatticeDev *L_dev, bool odd, int red, int k, const StepLaunch &ls,
                          cudaStream_t s) {
-  const bool w = (ls.row & 2) != 0, p512 = (ls.row & 4) != 0;
+  const bool w = (ls.row & 2) != 0, p512 = (ls.row & 4) != 0, tl = (ls.row & 8) != 0;
   if (p512) {
-    if (w) return launch_row_v<LAT, ST, true, 512, (MINB > 1 ? MINB - 1 : 1)>(L_dev, odd, red, k, ls, s);
-    return launch_row_v<LAT, ST, false, 512, (MINB > 1 ? MINB - 1 : 1)>(L_dev, odd, red, k, ls, s);
+    if (w) return launch_row_v<LAT, ST, true, 512, (MINB > 1 ? MINB - 1 : 1), false>(L_dev, odd, red, k, ls, s);
+    return launch_row_v<LAT, ST, false, 512, (MINB > 1 ? MINB - 1 : 1), false>(L_dev, odd, red, k, ls, s);
   }
-  if (w) return launch_row_v<LAT, ST, true, 256, MINB>(L_dev, odd, red, k, ls, s);
-  return launch_row_v<LAT, ST, false, 256, MINB>(L_dev, odd, red, k, ls, s);
+  if (tl) {
+    if (w) return launch_row_v<LAT, ST, true, 256, MINB, true>(L_dev, odd, red, k, ls, s);
+    return launch_row_v<LAT, ST, false, 256, MINB, true>(L_dev, odd, red, k, ls, s);
+  }
+  if (w) return launch_row_v<LAT, ST, true, 256, MINB, false>(L_dev, odd, red, k, ls, s);
+  return launch_row_v<LAT, ST, false, 256, MINB, false>(L_dev, odd, red, k, ls, s);
 }
 
-template <class LAT, class ST, bool W, int P, int MINB, bool ODD, bool RED, int RS, bool TUNED = false>
+template <class LAT, class ST, bool W, int P, int MINB, bool TL, bool ODD, bool RED, int RS, bool TUNED = false>
 cudaError_t configure_row_one(int smem) {
   using C = RowCfg<LAT, ST, P, MINB>;
-  return cudaFuncSetAttribute(step_row_kernel<LAT, ST, ODD, RED, W, P, C::kNS, MINB, RS, C::kNOut, TUNED>,
+  return cudaFuncSetAttribute(step_row_kernel<LAT, ST, ODD, RED, W, P, C::kNS, MINB, RS, C::kNOut, TL, TUNED>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
-template <class LAT, class ST, bool W, int P, int MINB>
+template <class LAT, class ST, bool W, int P, int MINB, bool TL>
 int configure_row_v(int &occ, int &nc, int &ns) {
   using C = RowCfg<LAT, ST, P, MINB>;
   static_assert(C::kNS >= 2, "a row kernel needs at least two stages");
@@ -891,7 +1048,7 @@ int configure_row_v(int &occ, int &nc, int &ns) {
   if (smem_max > 220 * 1024) return 0;
   cudaError_t e = cudaSuccess;
 #define LBM_CFG(ODD, RED, RS) \
-  if (e == cudaSuccess) e = configure_row_one<LAT, ST, W, P, MINB, ODD, RED, RS>(smem_max)
+  if (e == cudaSuccess) e = configure_row_one<LAT, ST, W, P, MINB, TL, ODD, RED, RS>(smem_max)
   LBM_CFG(true, false, 0);
   LBM_CFG(true, true, 0);
   LBM_CFG(false, false, 0);
@@ -901,16 +1058,17 @@ int configure_row_v(int &occ, int &nc, int &ns) {
   LBM_CFG(false, false, 1);
   LBM_CFG(false, true, 1);
 #undef LBM_CFG
-  if (e == cudaSuccess) e = configure_row_one<LAT, ST, W, P, MINB, true, false, 0, true>(smem_max);
-  if (e == cudaSuccess) e = configure_row_one<LAT, ST, W, P, MINB, false, false, 0, true>(smem_max);
+  if (e == cudaSuccess) e = configure_row_one<LAT, ST, W, P, MINB, TL, true, false, 0, true>(smem_max);
+  if (e == cudaSuccess) e = configure_row_one<LAT, ST, W, P, MINB, TL, false, false, 0, true>(smem_max);
   const int threads = (nc + (C::kNOut ? 2 : 1)) * 32;
   const int smem = ns * C::kIn + C::kNOut * C::kOut;
   const bool tuned = nc != C::kConsumers || ns != C::kNS;
   if (e == cudaSuccess)
     e = tuned ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                    &occ, step_row_kernel<LAT, ST, true, false, W, P, C::kNS, MINB, 0, C::kNOut, true>, threads, smem)
+                    &occ, step_row_kernel<LAT, ST, true, false, W, P, C::kNS, MINB, 0, C::kNOut, TL, true>, threads,
+                    smem)
               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                    &occ, step_row_kernel<LAT, ST, true, false, W, P, C::kNS, MINB, 0, C::kNOut>, threads, smem);
+                    &occ, step_row_kernel<LAT, ST, true, false, W, P, C::kNS, MINB, 0, C::kNOut, TL>, threads, smem);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -924,23 +1082,30 @@ int plan_row_t(int nx, int nxp, int ny, int nz, unsigned walls, StepLaunch &ls) 
   if ((long long)nxp * ny * nz > 0x7fffffffLL) return 0;  // int cell indices
   if (walls & 1u) return 0;
   const bool w = (walls & 6u) != 0, p512 = nxp > 256;
+  // rows of at most half the pitch are staged several at a time
+  const int R = p512 ? 1 : tile_rows(256, nxp);
+  const bool tl = R > 1;
   int occ = 0, ok, nc = ls.row_consumers, ns = ls.row_stages;
   if (p512)
-    ok = w ? configure_row_v<LAT, ST, true, 512, (MINB > 1 ? MINB - 1 : 1)>(occ, nc, ns)
-           : configure_row_v<LAT, ST, false, 512, (MINB > 1 ? MINB - 1 : 1)>(occ, nc, ns);
+    ok = w ? configure_row_v<LAT, ST, true, 512, (MINB > 1 ? MINB - 1 : 1), false>(occ, nc, ns)
+           : configure_row_v<LAT, ST, false, 512, (MINB > 1 ? MINB - 1 : 1), false>(occ, nc, ns);
+  else if (tl)
+    ok = w ? configure_row_v<LAT, ST, true, 256, MINB, true>(occ, nc, ns)
+           : configure_row_v<LAT, ST, false, 256, MINB, true>(occ, nc, ns);
   else
-    ok = w ? configure_row_v<LAT, ST, true, 256, MINB>(occ, nc, ns)
-           : configure_row_v<LAT, ST, false, 256, MINB>(occ, nc, ns);
+    ok = w ? configure_row_v<LAT, ST, true, 256, MINB, false>(occ, nc, ns)
+           : configure_row_v<LAT, ST, false, 256, MINB, false>(occ, nc, ns);
   if (!ok) return 0;
   ls.row_consumers = nc;
   ls.row_stages = ns;
   const int nyf = (walls & 2u) ? ny - 2 : ny;
   const int nzf = (walls & 4u) ? nz - 2 : nz;
-  const int nrows = nyf * nzf;
-  if (nrows < 1) return 0;
+  if (nyf < 1 || nzf < 1) return 0;
+  // work items: tiles of R rows of one plane
+  const long long ntiles = (long long)((nyf + R - 1) / R) * nzf;
   const int cap = sm_count() * occ;
-  ls.row = 1 | (w ? 2 : 0) | (p512 ? 4 : 0);
-  ls.row_grid = nrows < cap ? nrows : cap;
+  ls.row = 1 | (w ? 2 : 0) | (p512 ? 4 : 0) | (tl ? 8 : 0);
+  ls.row_grid = ntiles < cap ? (int)ntiles : cap;
   ls.row_smem_odd = ls.row_smem_even = 0;
   return 1;
 }

@@ -78,6 +78,22 @@ def eps_travelling_wave(L: int, t: float, T: float = 1000.0, mean: float = 0.7,
     return mean + a * np.sin(ph), a * np.cos(ph) * (2 * np.pi / T)
 
 
+def eps_travelling_wave_torch(L: int, t: float, T: float = 1000.0, mean: float = 0.7,
+                              amp: float = 0.2, device="cuda", dtype=None):
+    """eps_travelling_wave evaluated with torch on `device` (FP64, then cast
+    to `dtype`): flat (phi, d_t phi) of L^3 cells, x fastest."""
+    import torch
+    dtype = dtype or torch.float64
+    k = 2 * np.pi / L
+    r = torch.arange(L, dtype=torch.float64, device=device) * k
+    sx, cy = torch.sin(r), torch.cos(r)
+    ph = r + 2 * np.pi * t / T
+    a = (sx.reshape(1, 1, L) * cy.reshape(1, L, 1)) * amp
+    e = mean + a * torch.sin(ph).reshape(L, 1, 1)
+    d = a * torch.cos(ph).reshape(L, 1, 1) * (2 * np.pi / T)
+    return e.reshape(-1).to(dtype).contiguous(), d.reshape(-1).to(dtype).contiguous()
+
+
 def eps_product_sine(shape, amp: float) -> np.ndarray:
     """phi = (1 - amp) + amp prod_k sin(2 pi x_k / n_k) over the lattice's axes."""
     nz, ny, nx = shape
