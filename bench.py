@@ -79,7 +79,8 @@ def profiled_traffic(storage: str, kernel_src_hash: str):
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for name in ("step_row.cuh", "step_fast.cuh", "step_fast_d3q19.cu", "lattice.cuh", "internal.h"):
+    for name in ("step_row.cuh", "step_row_pair.cuh", "step_fast.cuh", "step_fast_d3q19.cu", "lattice.cuh",
+                 "internal.h"):
         with open(os.path.join(ROOT, "paper_2208_09267_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

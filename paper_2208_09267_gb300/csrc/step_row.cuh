@@ -45,6 +45,9 @@ namespace lbm {
 #ifndef LBM_ROW_CONSUMERS_F16
 #define LBM_ROW_CONSUMERS_F16 6
 #endif
+#ifndef LBM_ROW_OUTS_F16
+#define LBM_ROW_OUTS_F16 1  // FP16 rows written back through output stages (0: direct stores)
+#endif
 // Consumer warps per block (+ one producer warp).  Two blocks per SM (MINB
 // 2) take 7: every SM sub-partition then holds four warps of up to 128
 // registers.  Where a stage is too large for two blocks per SM (MINB 1: rows
@@ -740,7 +743,7 @@ struct RowCfg {
   static constexpr int kBudget = MINB > 1 ? 110 * 1024 : 216 * 1024;
   static constexpr int kMaxIn = MINB > 1 ? 3 : 6;
   static constexpr int kInWithOut = (kBudget - 2 * kOut) / kIn;
-  static constexpr bool kOuts = sizeof(ST) == 2 && kInWithOut >= 2;
+  static constexpr bool kOuts = LBM_ROW_OUTS_F16 && sizeof(ST) == 2 && kInWithOut >= 2;
   static constexpr int kInOnly = kBudget / kIn;
   static constexpr int kNS = kOuts ? (kInWithOut < kMaxIn ? kInWithOut : kMaxIn) : (kInOnly < kMaxIn ? kInOnly : kMaxIn);
   static constexpr int kNOut = kOuts ? 2 : 0;
