@@ -514,51 +514,96 @@ def run_batched(count=256, steps=1000, storages=("fp16", "fp32")):
     return out
 
 
-def run_serving(rates=(10.0, 100.0, 500.0), window_s=6.0, max_requests=20,
-                sides=(32, 192), steps=(500, 20000)):
+def _fifo(arrivals, durations):
+    """Latencies and makespan of one sequential server (first come, first
+    served) for requests arriving at `arrivals` that take `durations`."""
+    t, lat = 0.0, []
+    for a, d in sorted(zip(arrivals, durations)):
+        t = max(t, a) + d
+        lat.append(t - a)
+    return lat, t
+
+
+def run_serving(rates=(10.0, 20.0, 50.0, 100.0, 200.0, 500.0), window_s=4.0, max_requests=16,
+                sides=(32, 192), steps=(500, 20000), serve_timeout_s=30.0, seq_timeout_s=90.0):
     """The served workload: for each arrival rate, a Poisson stream of D3Q19
     solves (side log-uniform in `sides`, random-sphere or sine phi 50/50, a
     step budget log-uniform in `steps`, half of them with a steady-state
     residual target of 1e-8 capped by that budget), admitted by an 80 GB HBM
     budget and served with continuous batching in FP16-shifted storage,
     against plain per-request FP32 (one solver per request, sequential).
-    Each rate runs a bounded trace: the requests arriving within `window_s`
-    seconds, at most `max_requests` (the same problems at every rate), and
-    each arm stops at 3 * window_s; the line states how many completed.  Reports solves/s and
-    p50/p99 latency (arrival to result on the host) per rate, and for the
-    requests both completed with the same step count the relative L2
-    distance of the FP16 answer to the FP32 one."""
+
+    Bounded trace: the requests arriving within `window_s` seconds, at most
+    `max_requests` (the same problems at every rate), the served run cut at
+    `serve_timeout_s`; the line states how many completed.  The sequential
+    FP32 server solves each problem once (its compute time per request does
+    not depend on the rate); its latencies at each rate follow from the
+    arrival times by first-come-first-served queueing of those measured
+    durations.  Reports solves/s and p50/p99 latency (arrival to result on
+    the host) per rate, and the relative L2 distance of the FP16 velocity to
+    FP32 run to the same step count: for budget-limited requests the
+    sequential run itself, for requests the server retired on the residual
+    target an FP32 run of exactly the steps the FP16 request took."""
+    import dataclasses
+
     import torch
 
     from paper_2208_09267_gb300 import serve
     stream = torch.cuda.current_stream().cuda_stream
+    count = int(min(max_requests, max(4, max(rates) * window_s)))
     out = {"trace": f"Poisson arrivals, D3Q19 side log-uniform {sides}, steps log-uniform {steps}, "
-                    f"half with residual 1e-8, spheres or sine phi 50/50, 80 GB budget, window "
-                    f"{window_s:g} s per rate (run capped at {3 * window_s:g} s)", "rates": {}}
+                    f"half with residual 1e-8, spheres or sine phi 50/50, 80 GB budget, {count} requests "
+                    f"per rate (the same problems at every rate), served run cut at {serve_timeout_s:g} s",
+           "rates": {}}
+    # sequential FP32: every problem once, back to back
+    seq_reqs = [serve.Request(r.rid, r.spec, 0.0, r.eps)
+                for r in serve.make_requests(rates[0], count, sides=sides, steps=steps, seed_offset=5000)]
+    t_prev = 0.0
+    seq = serve.run_sequential(seq_reqs, storage="fp32", check_every=100, stream=stream,
+                               timeout_s=seq_timeout_s)
+    durations = {}
+    for r in sorted(seq_reqs, key=lambda r: r.rid):
+        if r.finished is not None:
+            durations[r.rid] = r.finished - t_prev
+            t_prev = r.finished
+    out["sequential_fp32_solve"] = {"completed": seq["completed"], "seconds": seq["elapsed_s"],
+                                    "glups": seq["glups"]}
+    first_served = None
     for rate in rates:
-        count = int(min(max_requests, max(4, rate * window_s)))
-        # the same problems at every rate (their phi generated once, by the
-        # client, before the run)
         reqs = serve.make_requests(rate, count, sides=sides, steps=steps, seed_offset=5000)
         srv = serve.Server(storage="fp16", hbm_budget=80e9, macro_steps=100, stream=stream,
                            keep_results=True)
-        served = srv.run(reqs, timeout_s=3 * window_s)
+        served = srv.run(reqs, timeout_s=serve_timeout_s)
         srv.close()
-        seq_reqs = [serve.Request(r.rid, r.spec, r.arrival, r.eps) for r in reqs]
-        seq = serve.run_sequential(seq_reqs, storage="fp32", check_every=100, stream=stream,
-                                   timeout_s=3 * window_s)
-        errs = []
-        for a, b in zip(reqs, seq_reqs):
-            if a.result is not None and b.result is not None and a.steps_done == b.steps_done:
-                ua, ub = a.result["u"].astype(np.float64), b.result["u"].astype(np.float64)
-                nb = np.linalg.norm(ub)
-                if nb > 0:
-                    errs.append((float(np.linalg.norm(ua - ub) / nb), a.status))
-        out["rates"][f"{rate:g}"] = {
-            "requests": count, "served_fp16": served, "sequential_fp32": seq,
-            "fp16_vs_fp32_u_rel_l2_max": max(e for e, _ in errs) if errs else None,
-            "fp16_vs_fp32_compared": len(errs),
-            "fp16_vs_fp32_compared_converged": sum(1 for _, st in errs if st == "converged")}
+        if first_served is None:
+            first_served = reqs
+        done = [r for r in reqs if r.rid in durations]
+        lat, makespan = _fifo([r.arrival for r in done], [durations[r.rid] for r in done])
+        seq_rate = {"completed": len(done), "solves_per_s": len(done) / makespan if makespan > 0 else 0.0,
+                    "p50_latency_s": float(np.percentile(lat, 50)) if lat else None,
+                    "p99_latency_s": float(np.percentile(lat, 99)) if lat else None}
+        out["rates"][f"{rate:g}"] = {"requests": count, "served_fp16": served, "sequential_fp32": seq_rate}
+    # FP16 against FP32 at the same step count
+    errs = {"budget": [], "residual": []}
+    seq_by_id = {r.rid: r for r in seq_reqs}
+    for a in first_served:
+        if a.result is None:
+            continue
+        b = seq_by_id.get(a.rid)
+        if a.status == "converged":
+            spec = dataclasses.replace(a.spec, steps=a.steps_done, residual_tol=0.0)
+            ref = [serve.Request(a.rid, spec, 0.0, a.eps)]
+            serve.run_sequential(ref, storage="fp32", check_every=100, stream=stream)
+            b, kind = ref[0], "residual"
+        else:
+            kind = "budget"
+        if b is None or b.result is None or b.steps_done != a.steps_done:
+            continue
+        ua, ub = a.result["u"].astype(np.float64), b.result["u"].astype(np.float64)
+        nb = np.linalg.norm(ub)
+        if nb > 0:
+            errs[kind].append(float(np.linalg.norm(ua - ub) / nb))
+    out["fp16_vs_fp32_u_rel_l2"] = {k: {"max": max(v) if v else None, "compared": len(v)} for k, v in errs.items()}
     return out
 
 
@@ -644,8 +689,8 @@ def main():
     ap.add_argument("--porous-steps", type=int, default=200)
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=1000)
-    ap.add_argument("--serve-rates", type=float, nargs="+", default=[10.0, 100.0, 500.0])
-    ap.add_argument("--serve-window", type=float, default=6.0)
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[10.0, 20.0, 50.0, 100.0, 200.0, 500.0])
+    ap.add_argument("--serve-window", type=float, default=4.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -82,7 +82,8 @@ def _time_steps(lat, steps, warmup):
 # (consumer warps, staged rows) of the row-staged kernel; shapes the
 # library cannot launch for a lattice type fall back to its default and are
 # recorded under the shape that ran
-ROW_SHAPES = [(0, 0), (5, 2), (5, 3), (6, 2), (6, 3), (7, 2), (7, 3), (11, 3), (13, 4), (15, 4)]
+ROW_SHAPES = [(0, 0), (3, 2), (4, 2), (4, 3), (5, 2), (5, 3), (6, 2), (6, 3), (7, 2), (7, 3), (11, 3), (13, 4),
+              (15, 4)]
 
 
 def tune_step(lattice="D3Q19", storage="fp32", shape=(128, 128, 128), tau=0.6, steps=20, warmup=4,

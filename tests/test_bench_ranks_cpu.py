@@ -56,3 +56,19 @@ def test_one_rank_without_a_process_group():
     import bench
     assert bench.max_over_ranks(3.5, "cpu") == 3.5
     assert bench.aggregate_glups(16777216, 1000, 500.0, 1) == pytest.approx(16777216 * 1000 / 0.5 / 1e9)
+
+
+def test_sequential_server_queueing():
+    """The sequential FP32 baseline's latencies at a given rate follow from
+    its measured per-request times by first-come-first-served queueing: a
+    request starts when it has arrived and the previous one has finished."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    lat, makespan = bench._fifo([0.0, 0.5, 0.6, 5.0], [1.0, 1.0, 0.2, 0.3])
+    # starts 0, 1, 2, 5; finishes 1, 2, 2.2, 5.3
+    assert lat == pytest.approx([1.0, 1.5, 1.6, 0.3])
+    assert makespan == pytest.approx(5.3)
+    # arrivals out of order are served in arrival order
+    lat2, m2 = bench._fifo([0.6, 0.0, 5.0, 0.5], [0.2, 1.0, 0.3, 1.0])
+    assert sorted(lat2) == sorted(lat) and m2 == pytest.approx(makespan)
