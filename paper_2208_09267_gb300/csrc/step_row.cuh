@@ -45,6 +45,9 @@ namespace lbm {
 #ifndef LBM_ROW_CONSUMERS_F16
 #define LBM_ROW_CONSUMERS_F16 6
 #endif
+#ifndef LBM_ROW_PRODUCERS
+#define LBM_ROW_PRODUCERS 1  // producer warps per block of the single-lattice row kernel (1 or 2)
+#endif
 #ifndef LBM_ROW_OUTS_F16
 #define LBM_ROW_OUTS_F16 1  // FP16 rows written back through output stages (0: direct stores)
 #endif
@@ -61,6 +64,11 @@ constexpr int row_consumers() {
 }
 template <int MINB>
 constexpr int row_threads() { return (row_consumers<MINB>() + 1) * 32; }
+// the single-lattice kernel: producer warps per block, and consumers (one
+// fewer per extra producer, so that the block keeps its warp count)
+constexpr int kRowProducers = LBM_ROW_PRODUCERS;
+template <int MINB, bool PAIR>
+constexpr int row_consumers_single() { return row_consumers<MINB, PAIR>() - (kRowProducers - 1); }
 // FP16 plain steps of D2Q9/D3Q19 update two adjacent cells per lane
 // (update_row_pair); D3Q27's larger state would spill
 template <class LAT, class ST>
@@ -747,8 +755,8 @@ struct RowCfg {
   static constexpr int kInOnly = kBudget / kIn;
   static constexpr int kNS = kOuts ? (kInWithOut < kMaxIn ? kInWithOut : kMaxIn) : (kInOnly < kMaxIn ? kInOnly : kMaxIn);
   static constexpr int kNOut = kOuts ? 2 : 0;
-  static constexpr int kConsumers = row_consumers<MINB, row_pair_lattice<LAT, ST>()>();
-  static constexpr int kThreads = (kConsumers + (kOuts ? 2 : 1)) * 32;
+  static constexpr int kConsumers = row_consumers_single<MINB, row_pair_lattice<LAT, ST>()>();
+  static constexpr int kThreads = (kConsumers + kRowProducers + (kOuts ? 1 : 0)) * 32;
   static constexpr int kSmem = kNS * kIn + kNOut * kOut;
 };
 
@@ -776,7 +784,8 @@ struct RowCfg {
 // the default, and only for plain steps.
 template <class LAT, class ST, bool ODD, bool RED, bool WALLS, int PITCH, int MAXSTAGE, int MINB, int RS, int NOUT,
           bool TILED, bool TUNED = false>
-__global__ void __launch_bounds__((row_consumers<MINB, row_pair_lattice<LAT, ST>()>() + (NOUT ? 2 : 1)) * 32, MINB)
+__global__ void __launch_bounds__((row_consumers_single<MINB, row_pair_lattice<LAT, ST>()>() + kRowProducers +
+                                   (NOUT ? 1 : 0)) * 32, MINB)
     step_row_kernel(const LatticeDev *__restrict__ Lp, int k, int nstage) {
   constexpr int Q = LAT::Q;
   using Lay = RowLayout<LAT, ST, ODD, PITCH>;
@@ -785,8 +794,8 @@ __global__ void __launch_bounds__((row_consumers<MINB, row_pair_lattice<LAT, ST>
   // (update_row_pair: bit-identical results, fewer instructions per cell)
   constexpr bool kPair = row_pair_lattice<LAT, ST>() && !RED && RS == 0;
   constexpr int kChunk = kPair ? 64 : 32;
-  const int kConsumerWarps =
-      TUNED ? (int)(blockDim.x >> 5) - (NOUT ? 2 : 1) : row_consumers<MINB, row_pair_lattice<LAT, ST>()>();
+  const int kConsumerWarps = TUNED ? (int)(blockDim.x >> 5) - kRowProducers - (NOUT ? 1 : 0)
+                                   : row_consumers_single<MINB, row_pair_lattice<LAT, ST>()>();
   const int NSTAGE = TUNED ? nstage : MAXSTAGE;
   const int kInRegion = NSTAGE * RowLayout<LAT, ST, true, PITCH>::kStageBytes;
   __shared__ LatticeDev Ls;
@@ -833,8 +842,10 @@ __global__ void __launch_bounds__((row_consumers<MINB, row_pair_lattice<LAT, ST>
 #pragma unroll
   for (int j = 0; j < kRedWidth; ++j) acc.v[j] = 0.0;
 
-  if (warp == kConsumerWarps) {
-    // ---------------- producer warp
+  if (warp >= kConsumerWarps && warp < kConsumerWarps + kRowProducers) {
+    // ---------------- producer warp p: tiles j = p, p + P, p + 2P, ... of the
+    // block (P producers), so that one warp's copy issue overlaps the other's
+    const int pw = warp - kConsumerWarps;
     const bool withhold = L.withhold_copies != 0;
     const int ny = L.ny, nz = L.nz, nxp = L.nxp;
     const unsigned walls = L.walls;
@@ -845,12 +856,14 @@ __global__ void __launch_bounds__((row_consumers<MINB, row_pair_lattice<LAT, ST>
                                                                tile_copy_bytes(c1, 1, nxp) - tile_copy_bytes(c1, 0, nxp));
     const unsigned fixed = __reduce_add_sync(0xffffffffu, tile_copy_bytes(c0, 0, nxp) + tile_copy_bytes(c1, 0, nxp));
     // tile it = blockIdx.x + j G is (ty, tz) = (it % tpp, it / tpp), carried
-    // incrementally from one tile of the block to the next
-    const int step_y = (int)(gridDim.x % (unsigned)tpp), step_z = (int)(gridDim.x / (unsigned)tpp);
-    int ty = (int)(blockIdx.x % (unsigned)tpp), tz = (int)(blockIdx.x / (unsigned)tpp);
-    int issued_upto = -1;  // last tile index j whose copies were issued
-    int j = 0;
-    for (int it = blockIdx.x; it < ntiles; it += gridDim.x, ++j) {
+    // incrementally from one tile of this producer to its next
+    const unsigned stride = (unsigned)kRowProducers * gridDim.x;
+    const int it0 = (int)blockIdx.x + pw * (int)gridDim.x;
+    const int step_y = (int)(stride % (unsigned)tpp), step_z = (int)(stride / (unsigned)tpp);
+    int ty = it0 % tpp, tz = it0 / tpp;
+    int issued_upto = -1;  // last tile index j whose copies this warp issued
+    int j = pw;
+    for (int it = it0; it < ntiles; it += (int)stride, j += kRowProducers) {
       const int s = j % NSTAGE;
       if (j >= NSTAGE) {
         // the consumers released tile j - NSTAGE from this stage
@@ -883,11 +896,12 @@ __global__ void __launch_bounds__((row_consumers<MINB, row_pair_lattice<LAT, ST>
       __syncwarp();
     }
     if (abort_flag && lane == 0) {
-      // drain: wait (full limit) for every stage whose copies may be in flight
-      for (int jj = issued_upto - NSTAGE + 1; jj <= issued_upto; ++jj)
-        if (jj >= 0) mbar_wait_bounded(&full[jj % NSTAGE], (unsigned)((jj / NSTAGE) & 1));
+      // drain: wait (full limit) for every stage whose copies this warp may
+      // still have in flight
+      for (int jj = issued_upto; jj >= 0 && jj > issued_upto - NSTAGE * kRowProducers; jj -= kRowProducers)
+        mbar_wait_bounded(&full[jj % NSTAGE], (unsigned)((jj / NSTAGE) & 1));
     }
-  } else if (NOUT > 0 && warp == kConsumerWarps + 1) {
+  } else if (NOUT > 0 && warp == kConsumerWarps + kRowProducers) {
     // ---------------- storer warp: lane i writes population i's block back
     int cy = 0, cz = 0;
     if (lane < Q) dir_yz<LAT>(lane, cy, cz);
@@ -991,7 +1005,7 @@ cudaError_t launch_row_rs(const LatticeDev *L_dev, bool odd, bool red, int k, co
   const int ns = ls.row_stages >= 2 && ls.row_stages <= NS ? ls.row_stages : NS;
   const dim3 grid(ls.row_grid);
   if (RS == 0 && !red && (nc != C::kConsumers || ns != NS)) {
-    const dim3 block((nc + (NO ? 2 : 1)) * 32);
+    const dim3 block((nc + kRowProducers + (NO ? 1 : 0)) * 32);
     const int smem = ns * C::kIn + NO * C::kOut;
     if (odd) step_row_kernel<LAT, ST, true, false, W, P, NS, MINB, RS, NO, TL, true><<<grid, block, smem, s>>>(L_dev, k, ns);
     else step_row_kernel<LAT, ST, false, false, W, P, NS, MINB, RS, NO, TL, true><<<grid, block, smem, s>>>(L_dev, k, ns);
@@ -1063,7 +1077,7 @@ int configure_row_v(int &occ, int &nc, int &ns) {
 #undef LBM_CFG
   if (e == cudaSuccess) e = configure_row_one<LAT, ST, W, P, MINB, TL, true, false, 0, true>(smem_max);
   if (e == cudaSuccess) e = configure_row_one<LAT, ST, W, P, MINB, TL, false, false, 0, true>(smem_max);
-  const int threads = (nc + (C::kNOut ? 2 : 1)) * 32;
+  const int threads = (nc + kRowProducers + (C::kNOut ? 1 : 0)) * 32;
   const int smem = ns * C::kIn + C::kNOut * C::kOut;
   const bool tuned = nc != C::kConsumers || ns != C::kNS;
   if (e == cudaSuccess)
