@@ -374,7 +374,12 @@ def _row_pair(lattice, shape, storage, walls, tv, steps_chunks, refresh=True):
     # rows that are not a whole number of 32-cell chunks or of 8-element
     # units (stored rows padded to the next multiple of 8)
     ("D3Q19", (45, 11, 9), 0), ("D3Q19", (100, 9, 7), 6), ("D2Q9", (77, 30, 1), 2),
-    ("D3Q27", (13, 8, 7), 0), ("D3Q19", (500, 4, 3), 0)])
+    ("D3Q27", (13, 8, 7), 0), ("D3Q19", (500, 4, 3), 0),
+    # tiles of several short rows whose halo rows wrap around at both ends
+    # (copies split into runs), the whole y extent in one tile, and tiles
+    # next to y and z walls
+    ("D2Q9", (40, 3, 1), 0), ("D3Q19", (24, 2, 3), 0), ("D3Q27", (16, 5, 4), 4),
+    ("D3Q19", (40, 7, 5), 2)])
 def test_row_kernel_matches_cell_kernel_and_oracle(lattice, shape, walls, storage):
     """The row-staged kernel (TMA bulk copies of whole rows) and the
     one-cell-per-thread kernel compute the same update: equal populations to
@@ -385,15 +390,18 @@ def test_row_kernel_matches_cell_kernel_and_oracle(lattice, shape, walls, storag
     if storage == "fp32":
         assert np.abs(pr - pc).max() <= 4e-6 * np.abs(pc).max()
     else:
-        # float rounding order differs between the kernels; in FP16 storage
-        # that can flip the last bit of a half, so compare the fields
+        # the two FP16 kernels pair their stochastic roundings differently,
+        # so they differ by their own rounding noise (on a lattice of a few
+        # hundred cells about 1e-3); each is held to the FP16 bar against
+        # the oracle below, and to the same bar against each other
         mc, mr = cell.moments(), row.moments()
-        assert rel_l2(mr["u"], mc["u"]) <= 1e-3
-        assert rel_l2(mr["p"] - mr["p"].mean(), mc["p"] - mc["p"].mean()) <= 1e-3
-    m = row.moments()
+        assert rel_l2(mr["u"], mc["u"]) <= TOL[storage]
+        assert rel_l2(mr["p"] - mr["p"].mean(), mc["p"] - mc["p"].mean()) <= TOL[storage]
     rho, p, u = oracle_moments(P, f, n)
-    assert rel_l2(m["u"], u) <= TOL[storage]
-    assert rel_l2(m["p"] - m["p"].mean(), p - p.mean()) <= TOL[storage]
+    for lat in (row, cell):
+        m = lat.moments()
+        assert rel_l2(m["u"], u) <= TOL[storage]
+        assert rel_l2(m["p"] - m["p"].mean(), p - p.mean()) <= TOL[storage]
 
 
 def test_row_kernel_wait_limit_reports_timeout():
