@@ -61,7 +61,8 @@ cudaError_t launch_step(const LatticeDev &h, const LatticeDev *L_dev, long long 
   if (ls.row) {
     // bit 1: this step decodes with the previous phi's shift (set_epsilon
     // since the last step); the row kernel is instantiated for both cases
-    const int rr = (red ? 1 : 0) | (h.sig_rd != h.sig_wr ? 2 : 0);
+    // bit 2: phi has no time derivative (a stage layout without d_t phi)
+    const int rr = (red ? 1 : 0) | (h.sig_rd != h.sig_wr ? 2 : 0) | (h.has_deps ? 0 : 4);
     switch (h.lattice) {
       case 0: return launch_step_row_d2q9(L_dev, h.storage, odd, rr, k, ls, s);
       case 1: return launch_step_row_d3q19(L_dev, h.storage, odd, rr, k, ls, s);

@@ -53,7 +53,7 @@ struct lbm_vanse {
   int *status = nullptr;
   lbm::StepLaunch ls;
   long long last_check_n = -1;
-  std::map<std::tuple<int, int>, cudaGraphExec_t> graphs;  // (parity, steps)
+  std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;  // (parity, steps, phi has d_t phi)
   std::string err;
   size_t field_elem = 4;  // bytes of one phi / force value on the device
   // a phi refresh staged into the spare buffers (lbm_vanse_stage_epsilon)
@@ -797,7 +797,8 @@ static int run_plain_steps(lbm_vanse_t h, int k) {
 }
 
 static int get_graph(lbm_vanse_t h, int parity, int steps, cudaGraphExec_t *out) {
-  auto key = std::make_tuple(parity, steps);
+  // the launches depend on whether phi has a time derivative (stage layout)
+  auto key = std::make_tuple(parity, steps, h->h.has_deps);
   auto it = h->graphs.find(key);
   if (it != h->graphs.end()) {
     *out = it->second;

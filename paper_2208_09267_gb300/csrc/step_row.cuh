@@ -758,6 +758,14 @@ struct RowCfg {
   static constexpr int kConsumers = row_consumers_single<MINB, row_pair_lattice<LAT, ST>()>();
   static constexpr int kThreads = (kConsumers + kRowProducers + (kOuts ? 1 : 0)) * 32;
   static constexpr int kSmem = kNS * kIn + kNOut * kOut;
+  // static phi (no d_t phi blocks): a stage ends where the d_t phi blocks
+  // would start; one-block-per-SM shapes then fit more stages in up to
+  // 226 KB (D3Q27 at pitch 512: 3 instead of 2)
+  static constexpr int kInS = RowLayout<LAT, ST, true, P>::kDepsOff;
+  static constexpr int kBudgetS = MINB > 1 ? kBudget : 226 * 1024;
+  static constexpr int kNSS0 = (kBudgetS - kNOut * kOut) / kInS;
+  static constexpr int kNSS = kNSS0 > kNS ? (kNSS0 < kMaxIn ? kNSS0 : kMaxIn) : kNS;
+  static constexpr int kSmemS = kNSS * kInS + kNOut * kOut;
 };
 
 // Warp-specialised row kernel.  Warp kConsumerWarps is the producer: it
@@ -786,7 +794,7 @@ template <class LAT, class ST, bool ODD, bool RED, bool WALLS, int PITCH, int MA
           bool TILED, bool TUNED = false>
 __global__ void __launch_bounds__((row_consumers_single<MINB, row_pair_lattice<LAT, ST>()>() + kRowProducers +
                                    (NOUT ? 1 : 0)) * 32, MINB)
-    step_row_kernel(const LatticeDev *__restrict__ Lp, int k, int nstage) {
+    step_row_kernel(const LatticeDev *__restrict__ Lp, int k, int nstage, int lay_static) {
   constexpr int Q = LAT::Q;
   using Lay = RowLayout<LAT, ST, ODD, PITCH>;
   constexpr int kOutBytes = (Q * PITCH * (int)sizeof(ST) + 127) / 128 * 128;
@@ -796,8 +804,15 @@ __global__ void __launch_bounds__((row_consumers_single<MINB, row_pair_lattice<L
   constexpr int kChunk = kPair ? 64 : 32;
   const int kConsumerWarps = TUNED ? (int)(blockDim.x >> 5) - kRowProducers - (NOUT ? 1 : 0)
                                    : row_consumers_single<MINB, row_pair_lattice<LAT, ST>()>();
-  const int NSTAGE = TUNED ? nstage : MAXSTAGE;
-  const int kInRegion = NSTAGE * RowLayout<LAT, ST, true, PITCH>::kStageBytes;
+  // input stages: MAXSTAGE is the static-phi count (RowCfg::kNSS); with
+  // lay_static (phi without d_t phi, set by the launch) stages end where the
+  // d_t phi blocks would start
+  using Cfg = RowCfg<LAT, ST, PITCH, MINB>;
+  const bool stat = Cfg::kNSS > Cfg::kNS && lay_static != 0;
+  const int NSTAGE = TUNED ? nstage : (stat ? Cfg::kNSS : Cfg::kNS);
+  const int kInStride = stat ? Lay::kDepsOff : Lay::kStageBytes;
+  const int kInRegion = NSTAGE * (stat ? RowLayout<LAT, ST, true, PITCH>::kDepsOff
+                                       : RowLayout<LAT, ST, true, PITCH>::kStageBytes);
   __shared__ LatticeDev Ls;
   __shared__ alignas(8) unsigned long long full[MAXSTAGE];
   __shared__ alignas(8) unsigned long long empty[MAXSTAGE];
@@ -827,6 +842,13 @@ __global__ void __launch_bounds__((row_consumers_single<MINB, row_pair_lattice<L
   }
   __syncthreads();
   const LatticeDev &L = Ls;
+  if (stat && L.has_deps) {
+    // launched for the static layout on a lattice whose phi has a time
+    // derivative (the host keys its graphs by that, so this does not
+    // happen): the d_t phi blocks would overrun a stage; report and leave
+    if (tid == 0) atomicExch(L.status, 1);
+    return;
+  }
   const bool wy = (L.walls & 2u) != 0, wz = (L.walls & 4u) != 0;
   const int y_first = wy ? 1 : 0, nyf = wy ? L.ny - 2 : L.ny;
   const int z_first = wz ? 1 : 0, nzf = wz ? L.nz - 2 : L.nz;
@@ -888,7 +910,7 @@ __global__ void __launch_bounds__((row_consumers_single<MINB, row_pair_lattice<L
       if (!withhold) {
         if (lane == 0) mbar_arrive_expect_tx(&full[s], bytes);
         __syncwarp();
-        unsigned char *stage = stages + s * Lay::kStageBytes;
+        unsigned char *stage = stages + s * kInStride;
         issue_tile_copy(c0, stage, &full[s], y0, z, nr, ny, nz, nxp, walls, spitch);
         issue_tile_copy(c1, stage, &full[s], y0, z, nr, ny, nz, nxp, walls, spitch);
         issued_upto = j;
@@ -963,7 +985,7 @@ __global__ void __launch_bounds__((row_consumers_single<MINB, row_pair_lattice<L
       // the consumer warps across tiles so that every warp gets the same share
       const int nch = nr * ncr;
       const int first = (warp - rot + kConsumerWarps) % kConsumerWarps;
-      const unsigned char *stage = stages + s * Lay::kStageBytes;
+      const unsigned char *stage = stages + s * kInStride;
       for (int c = first; c < nch; c += kConsumerWarps) {
         const int t = c / ncr, xc = c - t * ncr;
         if constexpr (kPair)
@@ -995,41 +1017,49 @@ namespace lbm {
 // pitch 512 (else 256), bit 3 = tiles of several rows (rows of at most half
 // the pitch).
 template <class LAT, class ST, bool W, int P, int MINB, int RS, bool TL>
-cudaError_t launch_row_rs(const LatticeDev *L_dev, bool odd, bool red, int k, const StepLaunch &ls,
+cudaError_t launch_row_rs(const LatticeDev *L_dev, bool odd, bool red, bool stat, int k, const StepLaunch &ls,
                           cudaStream_t s) {
   using C = RowCfg<LAT, ST, P, MINB>;
-  constexpr int NS = C::kNS, NO = C::kNOut;
+  constexpr int NS = C::kNSS, NO = C::kNOut;
+  // static phi with a larger stage count: the static layout (stat)
+  const bool st = stat && C::kNSS > C::kNS;
+  const int ns_def = st ? C::kNSS : C::kNS;
   // a tuned shape (row_consumers, row_stages) other than the default runs the
   // generic instantiation, for plain steps only
   const int nc = ls.row_consumers > 0 && ls.row_consumers <= C::kConsumers ? ls.row_consumers : C::kConsumers;
-  const int ns = ls.row_stages >= 2 && ls.row_stages <= NS ? ls.row_stages : NS;
+  // (a planned stage count equal to the default is the default)
+  const int ns = ls.row_stages >= 2 && ls.row_stages < C::kNS ? ls.row_stages : ns_def;
   const dim3 grid(ls.row_grid);
-  if (RS == 0 && !red && (nc != C::kConsumers || ns != NS)) {
+  const int lay = st ? 1 : 0;
+  if (RS == 0 && !red && (nc != C::kConsumers || ns != ns_def)) {
     const dim3 block((nc + kRowProducers + (NO ? 1 : 0)) * 32);
-    const int smem = ns * C::kIn + NO * C::kOut;
-    if (odd) step_row_kernel<LAT, ST, true, false, W, P, NS, MINB, RS, NO, TL, true><<<grid, block, smem, s>>>(L_dev, k, ns);
-    else step_row_kernel<LAT, ST, false, false, W, P, NS, MINB, RS, NO, TL, true><<<grid, block, smem, s>>>(L_dev, k, ns);
+    const int smem = ns * (st ? C::kInS : C::kIn) + NO * C::kOut;
+    if (odd)
+      step_row_kernel<LAT, ST, true, false, W, P, NS, MINB, RS, NO, TL, true><<<grid, block, smem, s>>>(L_dev, k, ns, lay);
+    else
+      step_row_kernel<LAT, ST, false, false, W, P, NS, MINB, RS, NO, TL, true><<<grid, block, smem, s>>>(L_dev, k, ns, lay);
     return cudaGetLastError();
   }
   const dim3 block(C::kThreads);
-  const int smem = C::kSmem;
+  const int smem = st ? C::kSmemS : C::kSmem;
   if (odd) {
-    if (red) step_row_kernel<LAT, ST, true, true, W, P, NS, MINB, RS, NO, TL><<<grid, block, smem, s>>>(L_dev, k, ns);
-    else step_row_kernel<LAT, ST, true, false, W, P, NS, MINB, RS, NO, TL><<<grid, block, smem, s>>>(L_dev, k, ns);
+    if (red) step_row_kernel<LAT, ST, true, true, W, P, NS, MINB, RS, NO, TL><<<grid, block, smem, s>>>(L_dev, k, ns, lay);
+    else step_row_kernel<LAT, ST, true, false, W, P, NS, MINB, RS, NO, TL><<<grid, block, smem, s>>>(L_dev, k, ns, lay);
   } else {
-    if (red) step_row_kernel<LAT, ST, false, true, W, P, NS, MINB, RS, NO, TL><<<grid, block, smem, s>>>(L_dev, k, ns);
-    else step_row_kernel<LAT, ST, false, false, W, P, NS, MINB, RS, NO, TL><<<grid, block, smem, s>>>(L_dev, k, ns);
+    if (red) step_row_kernel<LAT, ST, false, true, W, P, NS, MINB, RS, NO, TL><<<grid, block, smem, s>>>(L_dev, k, ns, lay);
+    else step_row_kernel<LAT, ST, false, false, W, P, NS, MINB, RS, NO, TL><<<grid, block, smem, s>>>(L_dev, k, ns, lay);
   }
   return cudaGetLastError();
 }
 
 // red: bit 0 a check step, bit 1 the step decodes with the shift of the
-// previous phi (the first step after a refresh)
+// previous phi (the first step after a refresh), bit 2 phi has no time
+// derivative (static layout where it fits more stages)
 template <class LAT, class ST, bool W, int P, int MINB, bool TL>
 cudaError_t launch_row_v(const LatticeDev *L_dev, bool odd, int red, int k, const StepLaunch &ls,
                          cudaStream_t s) {
-  if (red & 2) return launch_row_rs<LAT, ST, W, P, MINB, 1, TL>(L_dev, odd, (red & 1) != 0, k, ls, s);
-  return launch_row_rs<LAT, ST, W, P, MINB, 0, TL>(L_dev, odd, (red & 1) != 0, k, ls, s);
+  if (red & 2) return launch_row_rs<LAT, ST, W, P, MINB, 1, TL>(L_dev, odd, (red & 1) != 0, (red & 4) != 0, k, ls, s);
+  return launch_row_rs<LAT, ST, W, P, MINB, 0, TL>(L_dev, odd, (red & 1) != 0, (red & 4) != 0, k, ls, s);
 }
 
 template <class LAT, class ST, int MINB>
@@ -1051,7 +1081,7 @@ cudaError_t launch_row_t(const LatticeDev *L_dev, bool odd, int red, int k, cons
 template <class LAT, class ST, bool W, int P, int MINB, bool TL, bool ODD, bool RED, int RS, bool TUNED = false>
 cudaError_t configure_row_one(int smem) {
   using C = RowCfg<LAT, ST, P, MINB>;
-  return cudaFuncSetAttribute(step_row_kernel<LAT, ST, ODD, RED, W, P, C::kNS, MINB, RS, C::kNOut, TL, TUNED>,
+  return cudaFuncSetAttribute(step_row_kernel<LAT, ST, ODD, RED, W, P, C::kNSS, MINB, RS, C::kNOut, TL, TUNED>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
@@ -1061,8 +1091,8 @@ int configure_row_v(int &occ, int &nc, int &ns) {
   static_assert(C::kNS >= 2, "a row kernel needs at least two stages");
   nc = nc > 0 && nc <= C::kConsumers ? nc : C::kConsumers;
   ns = ns >= 2 && ns <= C::kNS ? ns : C::kNS;
-  const int smem_max = C::kSmem;
-  if (smem_max > 220 * 1024) return 0;
+  const int smem_max = C::kSmemS > C::kSmem ? C::kSmemS : C::kSmem;
+  if (smem_max > 226 * 1024) return 0;
   cudaError_t e = cudaSuccess;
 #define LBM_CFG(ODD, RED, RS) \
   if (e == cudaSuccess) e = configure_row_one<LAT, ST, W, P, MINB, TL, ODD, RED, RS>(smem_max)
@@ -1082,10 +1112,10 @@ int configure_row_v(int &occ, int &nc, int &ns) {
   const bool tuned = nc != C::kConsumers || ns != C::kNS;
   if (e == cudaSuccess)
     e = tuned ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                    &occ, step_row_kernel<LAT, ST, true, false, W, P, C::kNS, MINB, 0, C::kNOut, TL, true>, threads,
+                    &occ, step_row_kernel<LAT, ST, true, false, W, P, C::kNSS, MINB, 0, C::kNOut, TL, true>, threads,
                     smem)
               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                    &occ, step_row_kernel<LAT, ST, true, false, W, P, C::kNS, MINB, 0, C::kNOut, TL>, threads, smem);
+                    &occ, step_row_kernel<LAT, ST, true, false, W, P, C::kNSS, MINB, 0, C::kNOut, TL>, threads, smem);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 0;
