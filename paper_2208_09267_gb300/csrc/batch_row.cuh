@@ -247,11 +247,24 @@ __global__ void __launch_bounds__(BatchRowCfg<LAT, ST, P>::kThreads, MINB)
         }
         const long long n = Lm.n + k;
         const float dn = ctx[s].dn, dn_force = ctx[s].dn_force;
-        const int ncr = (Lm.nx + 31) >> 5;
+        // FP16 D2Q9/D3Q19 tiles without a check or a pending shift change
+        // update two cells per lane, as a lattice stepped alone does
+        // (update_row_pair: bit-identical to the one-cell update)
+        constexpr bool kPairOK = row_pair_lattice<LAT, ST>() && RS == 0;
+        const bool pair = kPairOK && !red;
+        const int ncr = pair ? (Lm.nx + 63) >> 6 : (Lm.nx + 31) >> 5;
         const int nch = ctx[s].nr * ncr;
         const int first = (warp - rot + kConsumerWarps) % kConsumerWarps;
         for (int c = first; c < nch; c += kConsumerWarps) {
-          const int t = c / ncr, x = ((c - t * ncr) << 5) + lane;
+          const int t = c / ncr, xc = c - t * ncr;
+          if constexpr (kPairOK) {
+            if (pair) {
+              update_row_pair<LAT, ODD, WALLS, P, false>(Lm, data, t, ctx[s].rc[t], n, dn, dn_force,
+                                                         (xc << 6) + 2 * lane, nullptr);
+              continue;
+            }
+          }
+          const int x = (xc << 5) + lane;
           if (red)
             update_row_chunk<LAT, ST, ODD, REDC, WALLS, P, RS>(Lm, data, t, ctx[s].rc[t], n, dn, dn_force, x, acc);
           else
