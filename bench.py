@@ -322,8 +322,8 @@ def run_gpu(args, rank, world):
 
     # end to end through the C ABI with host buffers (FP32).  The refreshes
     # reach the library the way a streaming application would hand them
-    # over: a producer (eight host threads) copies each refresh's phi_ref and
-    # d_t phi into a ring of three pinned buffers, ahead of use.  The main
+    # over: a producer (twelve host threads) copies each refresh's phi_ref and
+    # d_t phi into a ring of six pinned buffers, ahead of use.  The main
     # loop stages the next refresh (H2D copy and checks on the library's copy
     # stream), steps, and commits it, so the upload overlaps the steps.  A
     # fresh pinned buffer per refresh would instead pay the host-memory
@@ -332,7 +332,7 @@ def run_gpu(args, rank, world):
     e2e = None
     if not args.no_e2e:
         import queue
-        ring = 3
+        ring = 6
         st_e = torch.empty((ring, N), dtype=torch.float32, pin_memory=True)
         st_d = torch.empty((ring, N), dtype=torch.float32, pin_memory=True)
         st_e_np = [st_e[i].numpy() for i in range(ring)]
@@ -341,8 +341,9 @@ def run_gpu(args, rank, world):
         ready = queue.Queue()
 
         import concurrent.futures as cf
-        pool = cf.ThreadPoolExecutor(max_workers=8)
-        parts = [(i * N // 8, (i + 1) * N // 8) for i in range(8)]
+        nthr = 12
+        pool = cf.ThreadPoolExecutor(max_workers=nthr)
+        parts = [(i * N // nthr, (i + 1) * N // nthr) for i in range(nthr)]
 
         def producer(first, count):
             for q in range(count):
@@ -354,7 +355,7 @@ def run_gpu(args, rank, world):
                     a, b = ab
                     np.copyto(st_e_np[slot][a:b], src_e[a:b])
                     np.copyto(st_d_np[slot][a:b], src_d[a:b])
-                list(pool.map(fill, parts))   # eight host threads fill the slot
+                list(pool.map(fill, parts))   # the host threads fill the slot
                 ready.put(slot)
 
         lat = lbm.Lattice("D3Q19", (L, L, L), tau=TAU, storage=args.storages[0],
