@@ -134,3 +134,40 @@ def test_staged_refresh_call_order():
         f64.stage_epsilon(e, d, K)
     assert ex.value.code == EINVAL
     f64.close()
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_switching_between_static_and_varying_phi(storage):
+    """A lattice whose row kernel stages fewer, larger stages when phi has a
+    time derivative (D3Q27 rows of 320 cells: 2 stages, 3 without d_t phi)
+    steps through graph replays with static phi, then with a varying phi,
+    then static again: each phase takes the stage layout of its phi, and the
+    run equals the one-cell-per-thread kernel's (populations to float
+    rounding in FP32; the moments within the FP16 bar in FP16)."""
+    shape = (320, 5, 6)
+    nx, ny, nz = shape
+    rng = np.random.default_rng(5)
+    e0 = (0.6 + 0.3 * rng.random(nx * ny * nz)).astype(np.float32)
+    d1 = (1e-4 * rng.standard_normal(nx * ny * nz)).astype(np.float32)
+    lats = []
+    for kern in ("row", "cell"):
+        lat = lbm.Lattice("D3Q27", shape, tau=0.6, storage=storage, walls=4, kernel=kern, tuned=False)
+        assert lat.row_kernel == (kern == "row")
+        lat.set_epsilon(e0)
+        lat.set_force((1e-5, 0.0, 0.0))
+        lat.init_equilibrium()
+        lat.step(130, check_every=-1)             # graph replays, static phi
+        lat.set_epsilon(e0, d1, 130)
+        lat.step(130, check_every=-1)             # varying phi
+        lat.set_epsilon(np.clip(e0 + 130 * d1, 0.05, 1.0))
+        st = lat.step(131)                        # static again, ends with a check step
+        assert not st["nan_seen"]
+        lats.append(lat)
+    row, cell = lats
+    if storage == "fp32":
+        pr, pc = row.populations(), cell.populations()
+        assert np.abs(pr - pc).max() <= 4e-6 * np.abs(pc).max()
+    else:
+        mr, mc = row.moments(), cell.moments()
+        ur, uc = mr["u"].ravel(), mc["u"].ravel()
+        assert np.linalg.norm(ur - uc) <= 2e-3 * np.linalg.norm(uc)
