@@ -78,11 +78,16 @@ def profiled_traffic(storage: str, kernel_src_hash: str):
 
 
 def kernel_source_hash() -> str:
+    """Hash of the D3Q19 row kernel's sources with comments and blank space
+    removed: a profile stays valid across comment edits, not code edits."""
     h = hashlib.sha256()
     for name in ("step_row.cuh", "step_row_pair.cuh", "step_fast.cuh", "step_fast_d3q19.cu", "lattice.cuh",
                  "internal.h"):
-        with open(os.path.join(ROOT, "paper_2208_09267_gb300", "csrc", name), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2208_09267_gb300", "csrc", name)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

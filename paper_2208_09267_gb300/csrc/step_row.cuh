@@ -768,8 +768,10 @@ struct RowCfg {
   static constexpr int kSmemS = kNSS * kInS + kNOut * kOut;
 };
 
-// Warp-specialised row kernel.  Warp kConsumerWarps is the producer: it
-// stages tile j into stage j % NSTAGE once the consumers have released the
+// Warp-specialised row kernel.  Warps kConsumerWarps .. + kRowProducers - 1
+// are the producers (one by default; producer p takes the block's tiles j =
+// p, p + P, ...): a producer stages tile j into stage j % NSTAGE once the
+// consumers have released the
 // tile that used it before (empty barrier), writes the tile's row contexts
 // and arms the full barrier with the byte count of the copies.  Each
 // producer lane owns up to two blocks of the tile's copies, set up once per
@@ -779,11 +781,12 @@ struct RowCfg {
 // warp.
 // NOUT > 0: the consumers write the updated tile into output stage j % NOUT
 // (after the storer has released it: oempty), then arrive on ofull; the
-// storer warp (kConsumerWarps + 1) waits on ofull, copies the Q output blocks
+// storer warp (the one after the producers) waits on ofull, copies the Q output blocks
 // to their destination rows with bulk copies (lane i: population i), waits
 // until the copies have read the stage and releases it.  No block-wide
 // barrier is taken inside the loop.
-// TUNED = false: row_consumers() consumer warps and MAXSTAGE input stages,
+// TUNED = false: row_consumers_single() consumer warps and RowCfg's input
+// stages (kNS; kNSS when the launch asks for the static-phi layout),
 // compile-time constants (the default shape).  TUNED = true: the launch
 // chooses the consumer warps (blockDim.x / 32 minus the producer and storer
 // warps, at most the default) and the input stages `nstage` (2 <= nstage <=
