@@ -109,8 +109,10 @@ typedef struct {
                                when the handle would need more */
   int block_x, block_y;     /* thread-block shape of the one-cell-per-thread
                                step kernel; 0 = library default */
-  int kernel;               /* step kernel: 0 = automatic, 1 = one cell per
-                               thread, 2 = row-staged (whole x-rows staged in
+  int kernel;               /* step kernel: 0 = automatic (row-staged where
+                               it fits and nx >= 32, else one cell per
+                               thread), 1 = one cell per thread, 2 =
+                               row-staged (tiles of whole x-rows staged in
                                shared memory by TMA bulk copies; needs
                                8 <= nx <= 512, FP32 or FP16 storage and no
                                walls on x; LBM_EINVAL otherwise) */
@@ -119,8 +121,8 @@ typedef struct {
                                counter-based hash of cell and step, so runs
                                are reproducible), 1 = round to nearest */
   int quad_auto;            /* 1 = choose the quadrature rule from phi (Sec.
-                               2.2: D1Q3, D2Q5 or D3Q7 "by the number of
-                               directions in which phi varies"): every
+                               2.2: D1Q3, D2Q5 or D3Q7 according to how many
+                               axes phi varies along): every
                                set_epsilon / commit_epsilon scans phi_ref and
                                d_t phi on the device and sets quad_axes to the
                                axes along which a value differs from its

@@ -125,8 +125,8 @@ def quad_weights(quad_dim: int):
 
 
 def quadrature_axes(eps_ref, deps_dt=None, dims=3):
-    """The quadrature rule Sec. 2.2 selects "by the number of directions in
-    which phi varies": (quad_axes, quad_dim) with bit a set when phi_ref (or
+    """The quadrature rule of Sec. 2.2, chosen by how many axes phi varies
+    along: (quad_axes, quad_dim) with bit a set when phi_ref (or
     d_t phi) differs anywhere from its periodic neighbour along axis a < dims
     (exact comparison), and every axis when phi is uniform.  Fields have
     shape (nz, ny, nx)."""
