@@ -379,7 +379,9 @@ def _row_pair(lattice, shape, storage, walls, tv, steps_chunks, refresh=True):
     # (copies split into runs), the whole y extent in one tile, and tiles
     # next to y and z walls
     ("D2Q9", (40, 3, 1), 0), ("D3Q19", (24, 2, 3), 0), ("D3Q27", (16, 5, 4), 4),
-    ("D3Q19", (40, 7, 5), 2)])
+    ("D3Q19", (40, 7, 5), 2),
+    # rows wider than half the pitch but narrower than it (one-row tiles)
+    ("D3Q19", (200, 6, 5), 2)])
 def test_row_kernel_matches_cell_kernel_and_oracle(lattice, shape, walls, storage):
     """The row-staged kernel (TMA bulk copies of whole rows) and the
     one-cell-per-thread kernel compute the same update: equal populations to
