@@ -627,9 +627,10 @@ def cpu_baseline(sample_L=48, steps=None, budget_s=15.0, plan=True):
     """The FP64 oracle on the host cores, timed on a bounded sample of the
     same workload (a sample_L^3 lattice with the same phi recipe, all cores),
     and with `plan`, bounded samples of the other workloads: the 64^2 D2Q9
-    case run in full on one thread, the D3Q19 sample on one thread, a
-    D3Q27 porous-channel block (64 x 32 x 32, walls on y) and eight lattices
-    of the batched workload (a few steps each), all cores."""
+    case run in full on one thread, the D3Q19 sample on one thread, the
+    D3Q19 workload at 64^3 and 128^3, a D3Q27 porous-channel block (64 x 32
+    x 32, walls on y) and eight lattices of the batched workload (a few steps
+    each), all cores."""
     import oracle
     from paper_2208_09267_gb300 import inputs
     oracle.build()
@@ -656,6 +657,12 @@ def cpu_baseline(sample_L=48, steps=None, budget_s=15.0, plan=True):
     legs["d2q9_64x64_1000_steps_1_thread"] = _oracle_rate(P1, P1.init(), 1000, 1)[0]
     # the space-time varying D3Q19 sample on one thread, 10 steps
     legs[f"d3q19_{sample_L}^3_1_thread"] = _oracle_rate(P, f, 10, 1)[0]
+    # the travelling-wave workload at 64^3 and 128^3 (the coarse levels of
+    # its refinement study), a few steps each, all cores
+    for Ls, ks in ((64, 10), (128, 3)):
+        e2, d2 = eps_fields(Ls, 0)
+        P2 = oracle.Problem("D3Q19", Ls, Ls, Ls, tau=TAU, eps_ref=e2, deps_dt=d2, g=G)
+        legs[f"d3q19_{Ls}^3_all_cores"] = _oracle_rate(P2, P2.init(), ks, 0)[0]
     # a block of the porous channel: D3Q27, walls on y, static phi
     shape = (32, 32, 64)
     e3 = inputs.eps_random_spheres(shape, seed_offset=2, wall_axis=1)
