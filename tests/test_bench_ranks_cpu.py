@@ -72,3 +72,23 @@ def test_sequential_server_queueing():
     # arrivals out of order are served in arrival order
     lat2, m2 = bench._fifo([0.6, 0.0, 5.0, 0.5], [0.2, 1.0, 0.3, 1.0])
     assert sorted(lat2) == sorted(lat) and m2 == pytest.approx(makespan)
+
+
+def test_kernel_fingerprint_ignores_comments_not_code(tmp_path, monkeypatch):
+    """The source fingerprint that keeps a committed ncu summary valid
+    changes with the kernel's code, not with its comments."""
+    import shutil
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    src = os.path.join(ROOT, "paper_2208_09267_gb300", "csrc")
+    dst = tmp_path / "paper_2208_09267_gb300" / "csrc"
+    shutil.copytree(src, dst)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench.kernel_source_hash()
+    p = dst / "step_row.cuh"
+    text = p.read_text()
+    p.write_text(text.replace("#pragma once", "// a comment\n/* another\n   one */\n#pragma once", 1))
+    assert bench.kernel_source_hash() == h0
+    p.write_text(text.replace("kMaxTileRows = 8", "kMaxTileRows = 4", 1))
+    assert bench.kernel_source_hash() != h0
